@@ -1,0 +1,179 @@
+/*
+ * pns.h -- C ABI of the GB300 Rejection-Free Partial Neighbor Search sampler.
+ *
+ * Samples QUBO targets  pi(x) ~ exp(-beta (x^T Q x + b^T x)),  x in {0,1}^n,
+ * with the jump-chain samplers of Chen, Rosenthal, Dote, Tamura and
+ * Sheikholeslami, "Sampling via Rejection-Free Partial Neighbor Search":
+ *
+ *   PNS_METROPOLIS  Algorithm 1 (Sec. 1.1): one uniform Hamming-1 proposal,
+ *                   accepted w.p. min(1, exp(-beta Delta)); every record has M = 1.
+ *   PNS_RF          Algorithm 2 (Sec. 1.2): all n neighbours weighted
+ *                   (1/n) min(1, exp(-beta Delta)); the next state is drawn in
+ *                   proportion (Proposition 5's exponential race) and the
+ *                   current one is recorded with multiplicity M = 1 + Geom(p),
+ *                   p = sum of the weights (the jump chain of Eq. (2)).
+ *   PNS_BASIC       Algorithm 3 (Sec. 2): as RF over a fresh uniform k-subset
+ *                   each step, proposal 1/k on the subset.  Biased (Sec. 2.1-2.2).
+ *   PNS_UNBIASED    Algorithm 6 (Sec. 3.2): partial neighbour sets N_i used in
+ *                   turn for L0 original samples each; a move is taken only if
+ *                   its M fits the remaining budget L, else the state is
+ *                   recorded with M = L and the next set starts.  Systematic
+ *                   sets are k consecutive bits starting at (i k) mod n
+ *                   (Sec. 4-5, wrapping when k does not divide n); random sets
+ *                   are a fresh uniform k-subset each period (Sec. 5).
+ *
+ * Each step reads the flip deltas of the candidate bits from maintained local
+ * fields h = Q x + b,
+ *     Delta_i = s_i (2 h_i - b_i) + Q_ii,   s_i = 1 - 2 x_i,
+ * and a move to bit j updates all fields by the row Q[j,:] (rank-1 update).
+ * Integer QUBOs are computed exactly (int32 fields); fp32 QUBOs in fp32 with a
+ * fixed operation order.  Random numbers come from Philox4x32-10 with a fixed
+ * counter layout, so a chain's records depend only on (seed, chain id, inputs)
+ * and not on how chains are mapped onto the GPU.
+ *
+ * Replica exchange (parallel tempering, named in Sec. 4 as a way to use
+ * parallel hardware): when swap_interval > 0, the n_replicas chains of one
+ * (instance, chain) group run whole Unbiased periods and, every swap_interval
+ * original samples, adjacent temperatures swap with probability
+ * min(1, exp((beta_a - beta_b)(E_a - E_b))), alternating even / odd pairs.
+ *
+ * Pointers: every pointer argument may be host memory (pageable or pinned) or
+ * device memory of the context's device; the library detects which.  Nothing
+ * is retained after a call returns unless stated.  All functions return a
+ * pns_status; none aborts.  pns_last_error() gives a thread-local message for
+ * the last failing call.  Calls on one context must not overlap.
+ */
+#ifndef PNS_H
+#define PNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PNS_OK = 0,
+    PNS_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum or combination */
+    PNS_ERR_NOT_SYMMETRIC = 2, /* Q != Q^T (dense) or a CSR entry without its mirror */
+    PNS_ERR_RANGE = 3,         /* non-finite entry, or an integer field bound
+                                  3 * max_i (sum_j |Q_ij| + |b_i|) >= 2^31 */
+    PNS_ERR_OOM = 4,           /* device allocation failed */
+    PNS_ERR_CUDA = 5,          /* a CUDA call failed (message says which) */
+    PNS_ERR_TIMEOUT = 6,       /* a bounded device loop gave up (random subset draw) */
+    PNS_ERR_STATE = 7,         /* the context latched a device error: restore or destroy */
+    PNS_ERR_UNSUPPORTED = 8    /* valid request this build does not implement */
+} pns_status;
+
+typedef enum { PNS_BASIC = 0, PNS_UNBIASED = 1, PNS_RF = 2, PNS_METROPOLIS = 3 } pns_variant;
+typedef enum { PNS_Q_I16 = 0, PNS_Q_I32 = 1, PNS_Q_F32 = 2 } pns_qtype;
+typedef enum { PNS_DENSE = 0, PNS_CSR = 1 } pns_qformat;
+typedef enum { PNS_SUBSET_SYSTEMATIC = 0, PNS_SUBSET_RANDOM = 1 } pns_subset;
+
+/* One QUBO instance.  Q must be symmetric.  All instances of one context
+ * share qtype and fmt. */
+typedef struct {
+    int32_t n;                 /* bits, >= 1 */
+    int32_t fmt;               /* pns_qformat */
+    int32_t qtype;             /* pns_qtype of q, diag and b */
+    int32_t n_replicas;        /* temperatures of this instance (length of betas), >= 1 */
+    int32_t k;                 /* subset size for this instance (Basic, Unbiased); 0 = pns_config.k */
+    int32_t reserved;          /* must be 0 */
+    const void *q;             /* DENSE: n*n row-major; CSR: nnz off-diagonal values */
+    const int32_t *row_ptr;    /* CSR: n+1 offsets, row_ptr[0] = 0 */
+    const int32_t *col;        /* CSR: nnz column indices, no diagonal, no duplicates in a row */
+    int64_t nnz;               /* CSR: number of stored off-diagonal entries */
+    const void *diag;          /* CSR: n diagonal entries (NULL = 0); ignored for DENSE */
+    const void *b;             /* n linear terms (NULL = 0) */
+    const float *betas;        /* n_replicas inverse temperatures, finite, >= 0 */
+} pns_problem;
+
+typedef struct {
+    int32_t variant;           /* pns_variant */
+    int32_t k;                 /* |N_i|: 1..n (Basic, Unbiased); ignored for RF (k = n) and Metropolis */
+    int32_t subset;            /* pns_subset, Unbiased only */
+    int32_t chains_per_replica;/* independent chains per (instance, temperature), >= 1 */
+    int64_t L0;                /* Unbiased budget of original samples per set, >= 1 (paper: 100) */
+    int64_t swap_interval;     /* 0: no exchange; else original samples between exchange
+                                  rounds (Unbiased: a multiple of L0; Metropolis: any >= 1) */
+    uint64_t seed;             /* Philox key */
+    int32_t tape;              /* 0: no per-step records; 1: record (flip, M) every step */
+    int32_t warps_per_chain;   /* 0: choose automatically; else 1, 2, 4, 8, 16 or 32 */
+    const uint32_t *x0;        /* NULL (all zeros) or initial bit-packed states: chain c,
+                                  bit i at word c*W + i/32, bit i%32; W = pns_info.words_per_chain */
+} pns_config;
+
+/* Chain numbering: instance p, chain r of each temperature, replica slot s:
+ *   id = sum_{p' < p} chains_per_replica * n_replicas(p') + r * n_replicas(p) + s.
+ * Slot s starts at temperature index s; exchange moves temperatures, not states. */
+typedef struct {
+    int64_t chains;            /* total chains */
+    int32_t words_per_chain;   /* W: uint32 words per packed state (max n rounded up) */
+    int32_t field_stride;      /* elements per chain in pns_fields output */
+    int32_t field_bytes;       /* bytes per field element (1, 2, 4) */
+    int32_t field_is_float;    /* 1: fp32 fields, 0: signed integers */
+    int64_t tape_capacity;     /* records per chain held by the tape of the last pns_run */
+    int32_t warps_per_chain;   /* mapping in use */
+    int32_t ctas;              /* CTAs of the sampling launch */
+} pns_info;
+
+typedef struct {
+    int64_t steps;             /* records emitted so far (jump steps, stays included) */
+    int64_t flips;             /* moves */
+    int64_t stays;             /* Unbiased period ends, Metropolis rejections */
+    int64_t saturated;         /* moves whose M was clamped at 2^63 */
+    int64_t swaps_accepted;    /* exchanges this slot took part in */
+    int64_t budget_left;       /* Unbiased: L */
+    int64_t tape_records;      /* records written to the tape by the last pns_run */
+    int32_t set_start;         /* Unbiased systematic: first bit of the current set */
+    int32_t beta_idx;          /* temperature index currently held */
+    double energy;             /* E(x) of the current state */
+    double sum_m;              /* sum of M: original (Metropolis-equivalent) samples */
+    double best_energy;        /* lowest E seen */
+} pns_stats;
+
+typedef struct pns_ctx pns_ctx;
+
+/* Copies the instances (host or device memory) into library-owned device
+ * memory with padded rows, validates them on the device (symmetry, finiteness,
+ * integer field range), sets the initial states and computes h = Qx + b and E
+ * for every chain.  Enqueued on `stream` (a cudaStream_t, NULL = default) and
+ * synchronised before returning.  The caller may free its buffers afterwards. */
+pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_config *cfg, void *stream,
+                      pns_ctx **out);
+
+/* Runs every chain for `steps` more records (without exchange), or for `steps`
+ * more original samples, a multiple of swap_interval (with exchange).
+ * Asynchronous on `stream`; returns launch errors only.  With cfg.tape = 1 the
+ * records of this run replace the tape. */
+pns_status pns_run(pns_ctx *ctx, int64_t steps, void *stream);
+
+/* Synchronises `stream` and copies out: states (chains x W words), the tape
+ * (chains x tape_capacity M values and flip indices, -1 = stay; entries past a
+ * chain's tape_records are undefined) and per-chain statistics (host memory).
+ * Any pointer may be NULL.  Returns a device error latched by earlier runs. */
+pns_status pns_read(pns_ctx *ctx, uint32_t *states, double *multiplicities, int32_t *flips, pns_stats *stats,
+                    void *stream);
+
+/* Copies the maintained local fields h (chains x field_stride elements of
+ * field_bytes each, integers or fp32 per pns_info) to `out`. */
+pns_status pns_fields(pns_ctx *ctx, void *out, void *stream);
+
+pns_status pns_get_info(const pns_ctx *ctx, pns_info *info);
+
+/* Serialises every chain's state (statistics, bits, fields, exchange counters)
+ * into host memory.  With buf = NULL only *bytes is set.  Restoring it into a
+ * context created with the same problems and configuration continues the
+ * chains exactly as if they had not stopped. */
+pns_status pns_checkpoint(pns_ctx *ctx, void *buf, size_t *bytes);
+pns_status pns_restore(pns_ctx *ctx, const void *buf, size_t bytes);
+
+void pns_destroy(pns_ctx *ctx);
+const char *pns_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNS_H */

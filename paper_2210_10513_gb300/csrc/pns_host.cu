@@ -1,0 +1,698 @@
+// pns_host.cu -- the C ABI of include/pns.h: instance upload and validation,
+// chain-to-CTA planning, launches, read-back and checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pns.h"
+#include "pns_launch.h"
+
+using namespace pnsk;
+
+namespace {
+
+thread_local std::string g_err;
+
+pns_status fail(pns_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            if (e_ == cudaErrorMemoryAllocation)                                                   \
+                return fail(PNS_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_));                 \
+            return fail(PNS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                    \
+        }                                                                                          \
+    } while (0)
+
+int qtype_bytes(int qtype) { return qtype == PNS_Q_I16 ? 2 : 4; }
+
+int32_t round_up(int32_t v, int32_t m) { return (v + m - 1) / m * m; }
+
+struct InstHost {
+    int32_t n, ld, k, R;
+    int64_t q_off;       // elements (dense) / values (CSR) into the Q buffer
+    int64_t nnz;
+    int64_t rp_off;      // CSR row_ptr offset
+    int64_t vec_off;     // offset of diag / b (elements)
+    int64_t beta_off;
+};
+
+constexpr uint64_t kCkptMagic = 0x31504b4353504e50ull;  // "PNSCKP1"
+
+}  // namespace
+
+struct pns_ctx {
+    int device = 0;
+    pns_config cfg{};
+    int fmt = 0, qtype = 0, is_float = 0, hbytes = 4, T = 1;
+    std::vector<InstHost> inst;
+    int32_t max_ld = 32, LD = 32, W = 1;
+    int64_t chains = 0;
+    int R = 1;  // exchange group size
+    // device memory
+    void *d_q = nullptr;
+    int32_t *d_rowptr = nullptr, *d_col = nullptr;
+    void *d_diag = nullptr, *d_b = nullptr;
+    float *d_betas = nullptr;
+    InstDesc *d_inst = nullptr;
+    ChainDesc *d_chain = nullptr;
+    ChainState *d_state = nullptr;
+    uint32_t *d_x = nullptr;
+    void *d_fields = nullptr;
+    CtaDesc *d_cta = nullptr;
+    int32_t *d_cta_chains = nullptr;
+    int32_t *d_status = nullptr;
+    int32_t *d_tape_flip = nullptr;
+    double *d_tape_m = nullptr;
+    int64_t tape_alloc = 0;  // records per chain allocated
+    int64_t tape_cap = 0;    // records per chain of the last run
+    // plan
+    int n_cta = 0, block = 32;
+    size_t smem = 0;
+    int latched = 0;
+};
+
+namespace {
+
+void free_ctx(pns_ctx *c) {
+    if (!c) return;
+    void *ptrs[] = {c->d_q, c->d_rowptr, c->d_col, c->d_diag, c->d_b, c->d_betas, c->d_inst, c->d_chain,
+                    c->d_state, c->d_x, c->d_fields, c->d_cta, c->d_cta_chains, c->d_status, c->d_tape_flip,
+                    c->d_tape_m};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+pns_status check_args(const pns_problem *probs, int32_t n_probs, const pns_config *cfg) {
+    if (!probs || n_probs < 1) return fail(PNS_ERR_INVALID_ARG, "need at least one problem");
+    if (!cfg) return fail(PNS_ERR_INVALID_ARG, "cfg is NULL");
+    if (cfg->variant < PNS_BASIC || cfg->variant > PNS_METROPOLIS)
+        return fail(PNS_ERR_INVALID_ARG, "unknown variant %d", cfg->variant);
+    if (cfg->subset != PNS_SUBSET_SYSTEMATIC && cfg->subset != PNS_SUBSET_RANDOM)
+        return fail(PNS_ERR_INVALID_ARG, "unknown subset mode %d", cfg->subset);
+    if (cfg->chains_per_replica < 1) return fail(PNS_ERR_INVALID_ARG, "chains_per_replica must be >= 1");
+    if (cfg->L0 < 1) return fail(PNS_ERR_INVALID_ARG, "L0 must be >= 1");
+    if (cfg->tape != 0 && cfg->tape != 1) return fail(PNS_ERR_INVALID_ARG, "tape must be 0 or 1");
+    const int w = cfg->warps_per_chain;
+    if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32))
+        return fail(PNS_ERR_INVALID_ARG, "warps_per_chain must be 0, 1, 2, 4, 8, 16 or 32");
+    if (cfg->swap_interval < 0) return fail(PNS_ERR_INVALID_ARG, "swap_interval must be >= 0");
+    if (cfg->swap_interval > 0) {
+        if (cfg->variant != PNS_UNBIASED && cfg->variant != PNS_METROPOLIS)
+            return fail(PNS_ERR_INVALID_ARG, "replica exchange needs PNS_UNBIASED or PNS_METROPOLIS");
+        if (cfg->variant == PNS_UNBIASED && cfg->swap_interval % cfg->L0 != 0)
+            return fail(PNS_ERR_INVALID_ARG, "swap_interval must be a multiple of L0");
+    }
+    const int fmt = probs[0].fmt, qt = probs[0].qtype;
+    if (fmt != PNS_DENSE && fmt != PNS_CSR) return fail(PNS_ERR_INVALID_ARG, "unknown format %d", fmt);
+    if (qt < PNS_Q_I16 || qt > PNS_Q_F32) return fail(PNS_ERR_INVALID_ARG, "unknown qtype %d", qt);
+    const int R0 = probs[0].n_replicas;
+    for (int p = 0; p < n_probs; ++p) {
+        const pns_problem &pr = probs[p];
+        if (pr.fmt != fmt || pr.qtype != qt)
+            return fail(PNS_ERR_INVALID_ARG, "problem %d: all problems must share fmt and qtype", p);
+        if (pr.n < 1 || pr.n > (1 << 24)) return fail(PNS_ERR_INVALID_ARG, "problem %d: n = %d out of range", p, pr.n);
+        if (pr.n_replicas < 1 || !pr.betas)
+            return fail(PNS_ERR_INVALID_ARG, "problem %d: need n_replicas >= 1 and betas", p);
+        if (!pr.q && !(fmt == PNS_CSR && pr.nnz == 0)) return fail(PNS_ERR_INVALID_ARG, "problem %d: q is NULL", p);
+        if (fmt == PNS_CSR && (!pr.row_ptr || pr.nnz < 0 || (pr.nnz > 0 && !pr.col)))
+            return fail(PNS_ERR_INVALID_ARG, "problem %d: CSR needs row_ptr, col and nnz >= 0", p);
+        if (pr.k < 0 || pr.reserved != 0) return fail(PNS_ERR_INVALID_ARG, "problem %d: k < 0 or reserved != 0", p);
+        if (cfg->variant == PNS_BASIC || cfg->variant == PNS_UNBIASED) {
+            const int k = pr.k > 0 ? pr.k : cfg->k;
+            if (k < 1 || k > pr.n)
+                return fail(PNS_ERR_INVALID_ARG, "problem %d: k = %d must be in [1, n = %d]", p, k, pr.n);
+        }
+        if (cfg->swap_interval > 0 && pr.n_replicas != R0)
+            return fail(PNS_ERR_INVALID_ARG, "replica exchange needs the same n_replicas for every problem");
+        if (cfg->swap_interval > 0 && pr.n_replicas > 32)
+            return fail(PNS_ERR_UNSUPPORTED, "replica exchange supports at most 32 replicas");
+    }
+    return PNS_OK;
+}
+
+}  // namespace
+
+// Per-instance subset size: RF uses all n bits, Metropolis one; Basic and
+// Unbiased take the instance's k, or cfg.k when it is 0.
+static int32_t inst_k(const pns_config &cfg, const pns_problem &pr) {
+    if (cfg.variant == PNS_RF) return pr.n;
+    if (cfg.variant == PNS_METROPOLIS) return 1;
+    return pr.k > 0 ? pr.k : cfg.k;
+}
+
+struct PlanOut {
+    std::vector<CtaDesc> cta;
+    std::vector<int32_t> cta_chains;
+    std::vector<int32_t> smem_off;  // per chain
+    int block = 32;
+    size_t smem = 0;
+};
+
+// Packs chains (or whole exchange groups) into CTAs.  Units are placed in
+// decreasing order of shared-memory need; a CTA takes units until it reaches
+// the team limit, the shared-memory limit or its share of the work.
+static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, int num_sms, size_t smem_cap,
+                       int per_cta_override, PlanOut &out) {
+    const int T = c.T;
+    const bool list = needs_list(c.cfg.variant, c.cfg.subset);
+    const bool pt = c.cfg.swap_interval > 0;
+    const int teams_cap = T == 32 ? 1 : std::min(512 / (32 * T), T > 1 ? 15 : 16);
+    struct Unit {
+        int32_t first, count, bytes;
+    };
+    std::vector<Unit> units;
+    const int R = pt ? c.R : 1;
+    for (int64_t i = 0; i < c.chains; i += R) {
+        const InstHost &ih = c.inst[chains[i].inst];
+        const int32_t per = chain_smem(ih.ld, ih.k, c.hbytes, list).total;
+        units.push_back({static_cast<int32_t>(i), R, per * R});
+    }
+    if (R > teams_cap) return fail(PNS_ERR_UNSUPPORTED, "exchange group of %d chains exceeds %d teams per CTA", R, teams_cap);
+    std::stable_sort(units.begin(), units.end(), [](const Unit &a, const Unit &b) { return a.bytes > b.bytes; });
+    int64_t target = (static_cast<int64_t>(units.size()) + num_sms - 1) / num_sms;
+    if (per_cta_override > 0) target = per_cta_override;
+    if (target < 1) target = 1;
+    out.smem_off.assign(c.chains, 0);
+    size_t cur_bytes = 0;
+    int cur_teams = 0, cur_units = 0, cur_groups = 0;
+    auto close = [&]() {
+        if (cur_teams == 0) return;
+        CtaDesc d;
+        d.first = static_cast<int32_t>(out.cta_chains.size()) - cur_teams;
+        d.count = cur_teams;
+        d.groups = pt ? cur_groups : 0;
+        d.pad = 0;
+        out.cta.push_back(d);
+        out.smem = std::max(out.smem, cur_bytes);
+        cur_bytes = 0;
+        cur_teams = cur_units = cur_groups = 0;
+    };
+    for (const Unit &u : units) {
+        if (static_cast<size_t>(u.bytes) > smem_cap)
+            return fail(PNS_ERR_UNSUPPORTED, "a chain (or exchange group) needs %d bytes of shared memory, over %zu",
+                        u.bytes, smem_cap);
+        // named barriers: ids 1..teams for T > 1 teams, then one per exchange group; 15 at most
+        const bool bars_ok = !pt || (T == 1 ? cur_groups + 1 <= 15 : cur_teams + u.count + cur_groups + 1 <= 15);
+        const bool fits = cur_teams + u.count <= teams_cap && cur_bytes + u.bytes <= smem_cap && cur_units < target &&
+                          bars_ok;
+        if (!fits) close();
+        const int32_t per = u.bytes / u.count;
+        for (int s = 0; s < u.count; ++s) {
+            out.smem_off[u.first + s] = static_cast<int32_t>(cur_bytes) + s * per;
+            out.cta_chains.push_back(u.first + s);
+        }
+        cur_bytes += u.bytes;
+        cur_teams += u.count;
+        cur_units += 1;
+        cur_groups += 1;
+    }
+    close();
+    int max_teams = 0;
+    for (const CtaDesc &d : out.cta) max_teams = std::max(max_teams, static_cast<int>(d.count));
+    out.block = max_teams * 32 * T;
+    if (pt && T == 1) {
+        for (const CtaDesc &d : out.cta)
+            if (d.groups > 15) return fail(PNS_ERR_UNSUPPORTED, "too many exchange groups in one CTA");
+    }
+    return PNS_OK;
+}
+
+static int auto_warps(const pns_ctx &c) {
+    int kmax = 1;
+    for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
+    int T = 1;
+    if (c.fmt == PNS_DENSE) {
+        if (kmax > 1024) T = 8;
+        else if (kmax > 512) T = 4;
+        else if (kmax > 256) T = 2;
+    } else {
+        if (kmax >= 4096) T = 32;
+        else if (kmax >= 2048) T = 16;
+        else if (kmax >= 512) T = 8;
+        else if (kmax >= 128) T = 4;
+    }
+    return T;
+}
+
+extern "C" {
+
+const char *pns_last_error(void) { return g_err.c_str(); }
+
+void pns_destroy(pns_ctx *ctx) { free_ctx(ctx); }
+
+pns_status pns_get_info(const pns_ctx *ctx, pns_info *info) {
+    if (!ctx || !info) return fail(PNS_ERR_INVALID_ARG, "NULL argument");
+    info->chains = ctx->chains;
+    info->words_per_chain = ctx->W;
+    info->field_stride = ctx->LD;
+    info->field_bytes = ctx->hbytes;
+    info->field_is_float = ctx->is_float;
+    info->tape_capacity = ctx->tape_cap;
+    info->warps_per_chain = ctx->T;
+    info->ctas = ctx->n_cta;
+    return PNS_OK;
+}
+
+pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_config *cfg, void *stream,
+                      pns_ctx **out) {
+    if (!out) return fail(PNS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    pns_status st = check_args(probs, n_probs, cfg);
+    if (st != PNS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    pns_ctx *c = new pns_ctx();
+    struct Guard {
+        pns_ctx *c;
+        bool keep = false;
+        ~Guard() {
+            if (!keep) free_ctx(c);
+        }
+    } guard{c};
+
+    c->cfg = *cfg;
+    c->cfg.x0 = nullptr;
+    c->fmt = probs[0].fmt;
+    c->qtype = probs[0].qtype;
+    c->is_float = c->qtype == PNS_Q_F32;
+    CU(cudaGetDevice(&c->device));
+    int num_sms = 0, smem_optin = 0;
+    CU(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    CU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+
+    // ---- instance layout ----------------------------------------------------
+    const int qb = qtype_bytes(c->qtype);
+    const int vb = 4;  // CSR values, diag and b are stored as int32 or float
+    int64_t q_elems = 0, rp_elems = 0, vec_elems = 0, beta_elems = 0;
+    c->inst.resize(n_probs);
+    for (int p = 0; p < n_probs; ++p) {
+        InstHost &ih = c->inst[p];
+        ih.n = probs[p].n;
+        ih.ld = round_up(ih.n, 32);
+        ih.k = inst_k(*cfg, probs[p]);
+        ih.R = probs[p].n_replicas;
+        ih.nnz = probs[p].nnz;
+        ih.q_off = q_elems;
+        q_elems += c->fmt == PNS_DENSE ? static_cast<int64_t>(ih.n) * ih.ld : ih.nnz;
+        ih.rp_off = rp_elems;
+        rp_elems += c->fmt == PNS_CSR ? ih.n + 1 : 0;
+        ih.vec_off = vec_elems;
+        vec_elems += ih.ld;
+        ih.beta_off = beta_elems;
+        beta_elems += ih.R;
+        c->max_ld = std::max(c->max_ld, ih.ld);
+    }
+    c->LD = c->max_ld;
+    c->W = c->max_ld / 32;
+    c->R = probs[0].n_replicas;
+
+    // ---- upload ---------------------------------------------------------------
+    const size_t q_bytes = static_cast<size_t>(std::max<int64_t>(q_elems, 1)) * (c->fmt == PNS_DENSE ? qb : vb);
+    CU(cudaMalloc(&c->d_q, q_bytes));
+    CU(cudaMemsetAsync(c->d_q, 0, q_bytes, s));
+    CU(cudaMalloc(&c->d_diag, static_cast<size_t>(vec_elems) * vb));
+    CU(cudaMalloc(&c->d_b, static_cast<size_t>(vec_elems) * vb));
+    CU(cudaMemsetAsync(c->d_diag, 0, static_cast<size_t>(vec_elems) * vb, s));
+    CU(cudaMemsetAsync(c->d_b, 0, static_cast<size_t>(vec_elems) * vb, s));
+    CU(cudaMalloc(&c->d_betas, static_cast<size_t>(beta_elems) * sizeof(float)));
+    if (c->fmt == PNS_CSR) {
+        CU(cudaMalloc(&c->d_rowptr, static_cast<size_t>(rp_elems) * sizeof(int32_t)));
+        CU(cudaMalloc(&c->d_col, static_cast<size_t>(std::max<int64_t>(q_elems, 1)) * sizeof(int32_t)));
+    }
+    int32_t *d_flags = nullptr;
+    unsigned long long *d_bound = nullptr;
+    void *d_tmp = nullptr;
+    struct TmpFree {
+        void **a, **b, **t;
+        ~TmpFree() {
+            if (*a) cudaFree(*a);
+            if (*b) cudaFree(*b);
+            if (*t) cudaFree(*t);
+        }
+    } tmpfree{reinterpret_cast<void **>(&d_flags), reinterpret_cast<void **>(&d_bound), &d_tmp};
+    CU(cudaMalloc(&d_flags, sizeof(int32_t) * n_probs));
+    CU(cudaMalloc(&d_bound, sizeof(unsigned long long) * n_probs));
+    CU(cudaMemsetAsync(d_flags, 0, sizeof(int32_t) * n_probs, s));
+    CU(cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long) * n_probs, s));
+    int64_t max_n = 0, max_nnz = 0;
+    for (const InstHost &ih : c->inst) {
+        max_n = std::max<int64_t>(max_n, ih.n);
+        max_nnz = std::max<int64_t>(max_nnz, ih.nnz);
+    }
+    // scratch for raw b / diag / CSR values of one instance at a time
+    const size_t tmp_bytes = static_cast<size_t>(std::max<int64_t>({2 * max_n, max_nnz, 1})) * 4 + 64;
+    CU(cudaMalloc(&d_tmp, tmp_bytes));
+    char *tmp = static_cast<char *>(d_tmp);
+    for (int p = 0; p < n_probs; ++p) {
+        const pns_problem &pr = probs[p];
+        const InstHost &ih = c->inst[p];
+        CU(cudaMemcpyAsync(c->d_betas + ih.beta_off, pr.betas, sizeof(float) * ih.R, cudaMemcpyDefault, s));
+        char *diag_out = static_cast<char *>(c->d_diag) + ih.vec_off * vb;
+        char *b_out = static_cast<char *>(c->d_b) + ih.vec_off * vb;
+        if (c->fmt == PNS_DENSE) {
+            char *qd = static_cast<char *>(c->d_q) + ih.q_off * qb;
+            CU(cudaMemcpy2DAsync(qd, static_cast<size_t>(ih.ld) * qb, pr.q, static_cast<size_t>(ih.n) * qb,
+                                 static_cast<size_t>(ih.n) * qb, ih.n, cudaMemcpyDefault, s));
+            const void *braw = nullptr;
+            if (pr.b) {
+                CU(cudaMemcpyAsync(tmp, pr.b, static_cast<size_t>(ih.n) * qb, cudaMemcpyDefault, s));
+                braw = tmp;
+            }
+            CU(launch_prepare_dense(c->qtype, qd, ih.n, ih.ld, braw, diag_out, b_out, d_flags + p, d_bound + p, s));
+        } else {
+            CU(cudaMemcpyAsync(c->d_rowptr + ih.rp_off, pr.row_ptr, sizeof(int32_t) * (ih.n + 1), cudaMemcpyDefault, s));
+            char *vals = static_cast<char *>(c->d_q) + ih.q_off * vb;
+            if (ih.nnz > 0) {
+                CU(cudaMemcpyAsync(c->d_col + ih.q_off, pr.col, sizeof(int32_t) * ih.nnz, cudaMemcpyDefault, s));
+                CU(cudaMemcpyAsync(tmp, pr.q, static_cast<size_t>(ih.nnz) * qb, cudaMemcpyDefault, s));
+                CU(launch_convert(c->qtype, tmp, vals, ih.nnz, s));
+            }
+            // raw diag / b converted into the output arrays, then checked in place
+            if (pr.diag) {
+                CU(cudaMemcpyAsync(tmp, pr.diag, static_cast<size_t>(ih.n) * qb, cudaMemcpyDefault, s));
+                CU(launch_convert(c->qtype, tmp, diag_out, ih.n, s));
+            }
+            if (pr.b) {
+                CU(cudaMemcpyAsync(tmp, pr.b, static_cast<size_t>(ih.n) * qb, cudaMemcpyDefault, s));
+                CU(launch_convert(c->qtype, tmp, b_out, ih.n, s));
+            }
+            CU(launch_prepare_csr(c->is_float, c->d_rowptr + ih.rp_off, c->d_col + ih.q_off, vals, diag_out, b_out,
+                                  ih.n, ih.nnz, diag_out, b_out, d_flags + p, d_bound + p, s));
+        }
+        // the scratch buffer is reused by the next instance
+        CU(cudaStreamSynchronize(s));
+    }
+    std::vector<int32_t> flags(n_probs);
+    std::vector<unsigned long long> bound(n_probs);
+    CU(cudaMemcpyAsync(flags.data(), d_flags, sizeof(int32_t) * n_probs, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(bound.data(), d_bound, sizeof(unsigned long long) * n_probs, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    long long ibound = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        if (flags[p] & FLAG_BAD_CSR) return fail(PNS_ERR_INVALID_ARG, "problem %d: malformed CSR structure", p);
+        if (flags[p] & FLAG_NONFINITE) return fail(PNS_ERR_RANGE, "problem %d: non-finite entry", p);
+        if (flags[p] & FLAG_ASYM) return fail(PNS_ERR_NOT_SYMMETRIC, "problem %d: Q is not symmetric", p);
+        if (c->is_float) {
+            double v;
+            memcpy(&v, &bound[p], sizeof(double));
+            if (!(v < 1e30)) return fail(PNS_ERR_RANGE, "problem %d: field bound %g too large for fp32 fields", p, v);
+        } else {
+            const long long v = static_cast<long long>(bound[p]);
+            if (v > 715827882LL)
+                return fail(PNS_ERR_RANGE, "problem %d: 3 * field bound %lld reaches 2^31 (int32 deltas)", p, v);
+            ibound = std::max(ibound, v);
+        }
+    }
+    for (const InstHost &ih : c->inst) {
+        std::vector<float> b(ih.R);
+        CU(cudaMemcpy(b.data(), c->d_betas + ih.beta_off, sizeof(float) * ih.R, cudaMemcpyDeviceToHost));
+        for (float v : b)
+            if (!(v >= 0.0f) || !(v < 3.0e38f)) return fail(PNS_ERR_INVALID_ARG, "betas must be finite and >= 0");
+    }
+    // field storage width
+    if (c->is_float) c->hbytes = 4;
+    else if (c->fmt == PNS_DENSE) c->hbytes = 4;
+    else c->hbytes = ibound <= 127 ? 1 : (ibound <= 32767 ? 2 : 4);
+
+    // ---- instance descriptors ---------------------------------------------------
+    std::vector<InstDesc> idesc(n_probs);
+    for (int p = 0; p < n_probs; ++p) {
+        const InstHost &ih = c->inst[p];
+        InstDesc &d = idesc[p];
+        d.q = static_cast<char *>(c->d_q) + ih.q_off * (c->fmt == PNS_DENSE ? qb : vb);
+        d.row_ptr = c->fmt == PNS_CSR ? c->d_rowptr + ih.rp_off : nullptr;
+        d.col = c->fmt == PNS_CSR ? c->d_col + ih.q_off : nullptr;
+        d.diag = static_cast<char *>(c->d_diag) + ih.vec_off * vb;
+        d.b = static_cast<char *>(c->d_b) + ih.vec_off * vb;
+        d.betas = c->d_betas + ih.beta_off;
+        d.n = ih.n;
+        d.ld = ih.ld;
+        d.k = ih.k;
+        d.R = ih.R;
+    }
+    CU(cudaMalloc(&c->d_inst, sizeof(InstDesc) * n_probs));
+    CU(cudaMemcpyAsync(c->d_inst, idesc.data(), sizeof(InstDesc) * n_probs, cudaMemcpyHostToDevice, s));
+
+    // ---- chains -------------------------------------------------------------------
+    std::vector<ChainDesc> chains;
+    int32_t group = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        for (int r = 0; r < cfg->chains_per_replica; ++r, ++group) {
+            for (int sl = 0; sl < c->inst[p].R; ++sl) {
+                ChainDesc d;
+                d.inst = p;
+                d.slot = sl;
+                d.group = group;
+                d.smem_off = 0;
+                chains.push_back(d);
+            }
+        }
+    }
+    c->chains = static_cast<int64_t>(chains.size());
+    if (c->chains > (1ll << 31) - 1) return fail(PNS_ERR_INVALID_ARG, "too many chains");
+
+    // ---- mapping ------------------------------------------------------------------
+    c->T = cfg->warps_per_chain > 0 ? cfg->warps_per_chain : auto_warps(*c);
+    if (!sampler_supported(c->fmt, c->qtype, c->hbytes, c->T)) {
+        if (cfg->warps_per_chain > 0)
+            return fail(PNS_ERR_UNSUPPORTED, "warps_per_chain = %d is not built for this format", c->T);
+        c->T = 1;
+    }
+    PlanOut pl;
+    int per_cta = 0;
+    if (const char *e = getenv("PNS_CHAINS_PER_CTA")) per_cta = atoi(e);
+    st = plan(*c, chains, num_sms, static_cast<size_t>(smem_optin), per_cta, pl);
+    if (st != PNS_OK) return st;
+    for (int64_t i = 0; i < c->chains; ++i) chains[i].smem_off = pl.smem_off[i];
+    c->n_cta = static_cast<int>(pl.cta.size());
+    c->block = pl.block;
+    c->smem = pl.smem;
+    CU(cudaMalloc(&c->d_chain, sizeof(ChainDesc) * chains.size()));
+    CU(cudaMemcpyAsync(c->d_chain, chains.data(), sizeof(ChainDesc) * chains.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMalloc(&c->d_cta, sizeof(CtaDesc) * pl.cta.size()));
+    CU(cudaMemcpyAsync(c->d_cta, pl.cta.data(), sizeof(CtaDesc) * pl.cta.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMalloc(&c->d_cta_chains, sizeof(int32_t) * pl.cta_chains.size()));
+    CU(cudaMemcpyAsync(c->d_cta_chains, pl.cta_chains.data(), sizeof(int32_t) * pl.cta_chains.size(),
+                       cudaMemcpyHostToDevice, s));
+
+    // ---- chain state ------------------------------------------------------------------
+    CU(cudaMalloc(&c->d_state, sizeof(ChainState) * c->chains));
+    CU(cudaMalloc(&c->d_x, sizeof(uint32_t) * c->W * c->chains));
+    CU(cudaMalloc(&c->d_fields, static_cast<size_t>(c->hbytes) * c->LD * c->chains));
+    CU(cudaMalloc(&c->d_status, sizeof(int32_t)));
+    CU(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), s));
+    std::vector<uint32_t> x(static_cast<size_t>(c->W) * c->chains, 0u);
+    if (cfg->x0) {
+        CU(cudaMemcpyAsync(x.data(), cfg->x0, sizeof(uint32_t) * x.size(), cudaMemcpyDefault, s));
+        CU(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < c->chains; ++i) {
+            const int n = c->inst[chains[i].inst].n;
+            for (int w = 0; w < c->W; ++w) {
+                const int lo = w * 32;
+                uint32_t valid = lo >= n ? 0u : (n - lo >= 32 ? 0xFFFFFFFFu : ((1u << (n - lo)) - 1u));
+                if (x[i * c->W + w] & ~valid)
+                    return fail(PNS_ERR_INVALID_ARG, "x0 of chain %lld has bits set at or beyond n", (long long)i);
+            }
+        }
+    }
+    CU(cudaMemcpyAsync(c->d_x, x.data(), sizeof(uint32_t) * x.size(), cudaMemcpyHostToDevice, s));
+    std::vector<ChainState> cs(c->chains);
+    for (int64_t i = 0; i < c->chains; ++i) {
+        ChainState &z = cs[i];
+        memset(&z, 0, sizeof(z));
+        z.L = cfg->L0;
+        z.beta_idx = chains[i].slot;
+    }
+    CU(cudaMemcpyAsync(c->d_state, cs.data(), sizeof(ChainState) * cs.size(), cudaMemcpyHostToDevice, s));
+    CU(launch_init_fields(c->fmt, c->qtype, c->hbytes, c->d_inst, c->d_chain, c->d_x, c->d_fields, c->d_state,
+                          c->chains, c->W, c->LD, c->max_ld, s));
+    CU(cudaStreamSynchronize(s));
+    guard.keep = true;
+    *out = c;
+    return PNS_OK;
+}
+
+pns_status pns_run(pns_ctx *c, int64_t steps, void *stream) {
+    if (!c) return fail(PNS_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->latched) return fail(PNS_ERR_STATE, "context holds a device error (%d); restore or destroy", c->latched);
+    if (steps < 0) return fail(PNS_ERR_INVALID_ARG, "steps must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool pt = c->cfg.swap_interval > 0;
+    int64_t cap = steps;
+    if (pt) {
+        if (steps % c->cfg.swap_interval != 0)
+            return fail(PNS_ERR_INVALID_ARG, "with exchange, steps must be a multiple of swap_interval");
+        if (c->cfg.variant == PNS_UNBIASED) cap = steps / c->cfg.L0 * (c->cfg.L0 + 1);
+    }
+    if (steps == 0) return PNS_OK;
+    if (c->cfg.tape) {
+        if (cap > c->tape_alloc) {
+            if (c->d_tape_flip) cudaFree(c->d_tape_flip);
+            if (c->d_tape_m) cudaFree(c->d_tape_m);
+            c->d_tape_flip = nullptr;
+            c->d_tape_m = nullptr;
+            c->tape_alloc = 0;
+            CU(cudaMalloc(&c->d_tape_flip, sizeof(int32_t) * cap * c->chains));
+            CU(cudaMalloc(&c->d_tape_m, sizeof(double) * cap * c->chains));
+            c->tape_alloc = cap;
+        }
+        c->tape_cap = cap;
+    } else {
+        c->tape_cap = 0;
+    }
+    KParams P;
+    memset(&P, 0, sizeof(P));
+    P.inst = c->d_inst;
+    P.chain = c->d_chain;
+    P.cta = c->d_cta;
+    P.cta_chains = c->d_cta_chains;
+    P.state = c->d_state;
+    P.xbits = c->d_x;
+    P.fields = c->d_fields;
+    P.tape_flip = c->d_tape_flip;
+    P.tape_m = c->d_tape_m;
+    P.status = c->d_status;
+    P.tape_cap = c->tape_cap;
+    P.steps = steps;
+    P.L0 = c->cfg.L0;
+    P.swap_interval = c->cfg.swap_interval;
+    P.seed = c->cfg.seed;
+    P.variant = c->cfg.variant;
+    P.subset = c->cfg.subset;
+    P.W = c->W;
+    P.LD = c->LD;
+    P.R = pt ? c->R : 1;
+    P.pt = pt ? 1 : 0;
+    P.tape = c->cfg.tape;
+    CU(launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, P, c->n_cta, c->block, c->smem, s));
+    return PNS_OK;
+}
+
+static pns_status sync_and_check(pns_ctx *c, cudaStream_t s) {
+    CU(cudaStreamSynchronize(s));
+    int32_t code = 0;
+    CU(cudaMemcpy(&code, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (code != 0) {
+        c->latched = code;
+        return fail(static_cast<pns_status>(code), "device reported error %d (a bounded loop gave up)", code);
+    }
+    return PNS_OK;
+}
+
+pns_status pns_read(pns_ctx *c, uint32_t *states, double *mult, int32_t *flips, pns_stats *stats, void *stream) {
+    if (!c) return fail(PNS_ERR_INVALID_ARG, "ctx is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pns_status st = sync_and_check(c, s);
+    if (st != PNS_OK) return st;
+    if (c->latched) return fail(PNS_ERR_STATE, "context holds a device error");
+    if (states) CU(cudaMemcpyAsync(states, c->d_x, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDefault, s));
+    if ((mult || flips) && c->tape_cap > 0) {
+        if (mult) CU(cudaMemcpyAsync(mult, c->d_tape_m, sizeof(double) * c->tape_cap * c->chains, cudaMemcpyDefault, s));
+        if (flips)
+            CU(cudaMemcpyAsync(flips, c->d_tape_flip, sizeof(int32_t) * c->tape_cap * c->chains, cudaMemcpyDefault, s));
+    }
+    if (stats) {
+        std::vector<ChainState> cs(c->chains);
+        CU(cudaMemcpyAsync(cs.data(), c->d_state, sizeof(ChainState) * c->chains, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < c->chains; ++i) {
+            const ChainState &z = cs[i];
+            pns_stats &o = stats[i];
+            o.steps = z.step;
+            o.flips = z.flips;
+            o.stays = z.stays;
+            o.saturated = z.saturated;
+            o.swaps_accepted = z.swaps;
+            o.budget_left = z.L;
+            o.tape_records = z.tape_records;
+            o.set_start = z.set_start;
+            o.beta_idx = z.beta_idx;
+            o.energy = z.E;
+            o.sum_m = z.sum_m;
+            o.best_energy = z.best_E;
+        }
+    }
+    CU(cudaStreamSynchronize(s));
+    return PNS_OK;
+}
+
+pns_status pns_fields(pns_ctx *c, void *out, void *stream) {
+    if (!c || !out) return fail(PNS_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pns_status st = sync_and_check(c, s);
+    if (st != PNS_OK) return st;
+    CU(cudaMemcpyAsync(out, c->d_fields, static_cast<size_t>(c->hbytes) * c->LD * c->chains, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    return PNS_OK;
+}
+
+struct CkptHeader {
+    uint64_t magic;
+    int64_t chains;
+    int32_t W, LD, hbytes, fmt;
+};
+
+pns_status pns_checkpoint(pns_ctx *c, void *buf, size_t *bytes) {
+    if (!c || !bytes) return fail(PNS_ERR_INVALID_ARG, "NULL argument");
+    const size_t nbytes = sizeof(CkptHeader) + sizeof(ChainState) * c->chains + sizeof(uint32_t) * c->W * c->chains +
+                          static_cast<size_t>(c->hbytes) * c->LD * c->chains;
+    if (!buf) {
+        *bytes = nbytes;
+        return PNS_OK;
+    }
+    if (*bytes < nbytes) return fail(PNS_ERR_INVALID_ARG, "checkpoint buffer too small (%zu < %zu)", *bytes, nbytes);
+    pns_status st = sync_and_check(c, nullptr);
+    if (st != PNS_OK) return st;
+    CU(cudaDeviceSynchronize());
+    char *p = static_cast<char *>(buf);
+    CkptHeader h{kCkptMagic, c->chains, c->W, c->LD, c->hbytes, c->fmt};
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    CU(cudaMemcpy(p, c->d_state, sizeof(ChainState) * c->chains, cudaMemcpyDefault));
+    p += sizeof(ChainState) * c->chains;
+    CU(cudaMemcpy(p, c->d_x, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDefault));
+    p += sizeof(uint32_t) * c->W * c->chains;
+    CU(cudaMemcpy(p, c->d_fields, static_cast<size_t>(c->hbytes) * c->LD * c->chains, cudaMemcpyDefault));
+    *bytes = nbytes;
+    return PNS_OK;
+}
+
+pns_status pns_restore(pns_ctx *c, const void *buf, size_t bytes) {
+    if (!c || !buf) return fail(PNS_ERR_INVALID_ARG, "NULL argument");
+    CkptHeader h;
+    if (bytes < sizeof(h)) return fail(PNS_ERR_INVALID_ARG, "checkpoint too short");
+    memcpy(&h, buf, sizeof(h));
+    const size_t nbytes = sizeof(CkptHeader) + sizeof(ChainState) * c->chains + sizeof(uint32_t) * c->W * c->chains +
+                          static_cast<size_t>(c->hbytes) * c->LD * c->chains;
+    if (h.magic != kCkptMagic || h.chains != c->chains || h.W != c->W || h.LD != c->LD || h.hbytes != c->hbytes ||
+        h.fmt != c->fmt || bytes != nbytes)
+        return fail(PNS_ERR_INVALID_ARG, "checkpoint does not match this context");
+    CU(cudaDeviceSynchronize());
+    const char *p = static_cast<const char *>(buf) + sizeof(h);
+    CU(cudaMemcpy(c->d_state, p, sizeof(ChainState) * c->chains, cudaMemcpyDefault));
+    p += sizeof(ChainState) * c->chains;
+    CU(cudaMemcpy(c->d_x, p, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDefault));
+    p += sizeof(uint32_t) * c->W * c->chains;
+    CU(cudaMemcpy(c->d_fields, p, static_cast<size_t>(c->hbytes) * c->LD * c->chains, cudaMemcpyDefault));
+    CU(cudaMemset(c->d_status, 0, sizeof(int32_t)));
+    c->latched = 0;
+    return PNS_OK;
+}
+
+}  // extern "C"

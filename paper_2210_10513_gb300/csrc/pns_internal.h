@@ -1,0 +1,110 @@
+// pns_internal.h -- descriptors shared by the host planner and the sm_103a
+// kernels of libpns.  Not part of the public ABI (include/pns.h is).
+#pragma once
+
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define PNS_HD __host__ __device__ __forceinline__
+#else
+#define PNS_HD inline
+#endif
+
+namespace pnsk {
+
+enum : int { VAR_BASIC = 0, VAR_UNBIASED = 1, VAR_RF = 2, VAR_METROPOLIS = 3 };
+enum : int { SUB_SYSTEMATIC = 0, SUB_RANDOM = 1 };
+
+// Philox stream tags (counter word 3, bits 24..31).
+enum : uint32_t { TAG_RACE = 1, TAG_STEP = 2, TAG_SUBSET = 3, TAG_SWAP = 5 };
+
+// Device status codes (mirror pns_status values).
+enum : int { ST_OK = 0, ST_TIMEOUT = 6 };
+
+// One QUBO instance as the kernels see it.
+struct InstDesc {
+    const void *q;          // dense: n rows of `ld` elements (zero padded); CSR: nnz values
+    const int32_t *row_ptr; // CSR only
+    const int32_t *col;     // CSR only
+    const void *diag;       // n diagonal entries: int32 (integer QUBO) or float
+    const void *b;          // n linear terms, same type as diag (zeros when absent)
+    const float *betas;     // R inverse temperatures
+    int32_t n, ld, k, R;
+};
+
+// One chain.
+struct ChainDesc {
+    int32_t inst;           // instance index
+    int32_t slot;           // replica slot inside its exchange group
+    int32_t group;          // global exchange group id
+    int32_t smem_off;       // byte offset of the chain's area in its CTA's shared memory
+};
+
+// One CTA of the sampling launch.
+struct CtaDesc {
+    int32_t first;          // first entry in the CTA chain list
+    int32_t count;          // chains (teams) in this CTA
+    int32_t groups;         // exchange groups in this CTA (count / R when exchanging)
+    int32_t pad;
+};
+
+// Persistent per-chain state in global memory (96 bytes).
+struct ChainState {
+    int64_t step;           // records emitted
+    int64_t L;              // Unbiased budget left
+    int64_t period_start;   // step at which the current random set was drawn
+    int64_t flips, stays, saturated, swaps, tape_records;
+    int32_t set_start;      // systematic set start bit
+    int32_t beta_idx;       // temperature index held
+    double E, sum_m, best_E;
+};
+static_assert(sizeof(ChainState) == 96, "ChainState layout");
+
+// Kernel parameters (passed by value).
+struct KParams {
+    const InstDesc *inst;
+    const ChainDesc *chain;
+    const CtaDesc *cta;
+    const int32_t *cta_chains;
+    ChainState *state;
+    uint32_t *xbits;        // chain c at c * W words
+    void *fields;           // chain c at c * LD elements
+    int32_t *tape_flip;     // chain c at c * tape_cap
+    double *tape_m;
+    int32_t *status;        // device status word (first error wins)
+    int64_t tape_cap;
+    int64_t steps;          // records (no exchange) or original samples (exchange)
+    int64_t L0;
+    int64_t swap_interval;
+    uint64_t seed;
+    int32_t variant, subset, W, LD;
+    int32_t R;              // chains per exchange group (1 without exchange)
+    int32_t pt;             // exchange on
+    int32_t tape;
+    int32_t pad;
+};
+
+PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }
+
+// Byte layout of one chain's shared-memory area.  Both the planner and the
+// kernel derive it from (ld, k, field bytes, whether a subset list is kept).
+struct ChainSmem {
+    int32_t fields, xw, list, bitmap, scratch, total;
+};
+
+PNS_HD ChainSmem chain_smem(int32_t ld, int32_t k, int32_t hbytes, bool list) {
+    ChainSmem s;
+    s.fields = 0;
+    s.xw = round16(ld * hbytes);
+    s.list = s.xw + round16(ld / 8);
+    s.bitmap = s.list + (list ? round16(k * 4) : 0);
+    s.scratch = s.bitmap + (list ? round16(ld / 8) : 0);
+    s.total = s.scratch + 768;   // 5 partials x 32 warps x 4 B, then the exchange publish slot
+    return s;
+}
+
+PNS_HD bool needs_list(int variant, int subset) {
+    return variant == VAR_BASIC || (variant == VAR_UNBIASED && subset == SUB_RANDOM);
+}
+
+}  // namespace pnsk

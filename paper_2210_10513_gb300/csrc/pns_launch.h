@@ -1,0 +1,41 @@
+// pns_launch.h -- host-side entry points of the kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pns_internal.h"
+
+namespace pnsk {
+
+// Validation flags written by the check kernels.
+enum : int32_t { FLAG_ASYM = 1, FLAG_NONFINITE = 2, FLAG_BAD_CSR = 4 };
+
+// Sampling launch.  fmt: 0 dense, 1 CSR.  qtype: 0 int16, 1 int32, 2 fp32.
+// hbytes: field element bytes (dense integer: 4; CSR integer: 1, 2 or 4; fp32: 4).
+// T: warps per chain.
+cudaError_t launch_sampler(int fmt, int qtype, int hbytes, int T, const KParams &P, int grid, int block,
+                           size_t smem, cudaStream_t s);
+bool sampler_supported(int fmt, int qtype, int hbytes, int T);
+
+// Dense instance set-up: validates the padded copy `q` (n rows of ld
+// elements of qtype) and the raw linear term `b_raw` (qtype, may be null);
+// writes diag / b as int32 (integer) or float, the row bound
+// max_i (sum_j |Q_ij| + |b_i|) (integer: exact; fp32: as double bits) and
+// flags.
+cudaError_t launch_prepare_dense(int qtype, const void *q, int n, int ld, const void *b_raw, void *diag_out,
+                                 void *b_out, int32_t *flags, unsigned long long *bound, cudaStream_t s);
+// CSR instance set-up: values are stored as int32 or float already.
+cudaError_t launch_prepare_csr(int is_float, const int32_t *row_ptr, const int32_t *col, const void *val,
+                               const void *diag_raw, const void *b_raw, int n, int64_t nnz, void *diag_out,
+                               void *b_out, int32_t *flags, unsigned long long *bound, cudaStream_t s);
+// Convert raw values of qtype into int32 / float.
+cudaError_t launch_convert(int qtype, const void *src, void *dst, int64_t count, cudaStream_t s);
+
+// Fields h = Qx + b and energies for chains [0, chains).
+cudaError_t launch_init_fields(int fmt, int qtype, int hbytes, const InstDesc *inst, const ChainDesc *chain,
+                               const uint32_t *xbits, void *fields, ChainState *state, int64_t chains, int W,
+                               int LD, int max_ld, cudaStream_t s);
+
+}  // namespace pnsk

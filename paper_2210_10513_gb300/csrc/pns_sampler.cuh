@@ -1,0 +1,514 @@
+// pns_sampler.cuh -- the persistent batched sampling kernel.
+//
+// One "team" of T warps owns one chain for the whole launch.  The chain's
+// local fields h = Qx + b and its packed bits live in shared memory; the
+// instance's Q rows stream from HBM / L2 with 16-byte non-coherent loads.  A
+// CTA holds several teams (several chains, or the replicas of exchange
+// groups), packed by the host planner.  Per record:
+//
+//   a1  candidate set N_i: systematic window, drawn k-subset, all bits (RF)
+//   a2  Delta_t = s_i (2 h_i - b_i) + Q_ii for each candidate (shared memory)
+//   a3  anchor A = min_t max(Delta_t, 0)                  (team min-reduction)
+//   a4  w_t = e^{-beta (Delta+_t - A)}, race key E_t / w_t (Proposition 5),
+//       S = sum_t floor(w_t 2^32)                         (order-free reductions)
+//   a5  p = (S 2^-32 / k) e^{-beta A}, M = 1 + Geom(p); Unbiased budget test
+//   a6  move: h += s_j Q[j, :], x_j ^= 1, E += Delta_j
+//   a7  record (j or -1, M) to the tape
+//   a8  (exchange) at period ends all replicas of a group meet at a named
+//       barrier and adjacent temperatures swap.
+//
+// Reductions are integer (min / add) or lexicographic (key, position), so a
+// chain's records do not depend on T or on how chains are packed.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "pns_device.cuh"
+#include "pns_internal.h"
+
+namespace pnsk {
+
+// ---------------------------------------------------------------------------
+// Type helpers: integer QUBOs compute deltas in int32, fp32 QUBOs in float.
+// ---------------------------------------------------------------------------
+template <typename HT> struct Arith;
+template <> struct Arith<float> {
+    using D = float;     // delta type
+    using C = float;     // type of b and diag arrays
+    static __device__ __forceinline__ float delta(float h, float b, float d, bool x) {
+        float g = __fsub_rn(__fadd_rn(h, h), b);
+        if (x) g = -g;
+        return __fadd_rn(g, d);
+    }
+    static __device__ __forceinline__ float pos(float v) { return v > 0.0f ? v : 0.0f; }
+    static __device__ __forceinline__ uint32_t key(float v) { return __float_as_uint(v); }  // v >= 0
+    static __device__ __forceinline__ float unkey(uint32_t u) { return __uint_as_float(u); }
+    static __device__ __forceinline__ float diff(float a, float m) { return __fsub_rn(a, m); }
+    static __device__ __forceinline__ float tof(float v) { return v; }
+    static __device__ __forceinline__ double tod(float v) { return static_cast<double>(v); }
+};
+template <typename HT> struct ArithInt {
+    using D = int32_t;
+    using C = int32_t;
+    static __device__ __forceinline__ int32_t delta(HT h, int32_t b, int32_t d, bool x) {
+        int32_t g = 2 * static_cast<int32_t>(h) - b;
+        if (x) g = -g;
+        return g + d;
+    }
+    static __device__ __forceinline__ int32_t pos(int32_t v) { return v > 0 ? v : 0; }
+    static __device__ __forceinline__ uint32_t key(int32_t v) { return static_cast<uint32_t>(v); }  // v >= 0
+    static __device__ __forceinline__ int32_t unkey(uint32_t u) { return static_cast<int32_t>(u); }
+    static __device__ __forceinline__ float diff(int32_t a, int32_t m) { return __int2float_rn(a - m); }
+    static __device__ __forceinline__ float tof(int32_t v) { return __int2float_rn(v); }
+    static __device__ __forceinline__ double tod(int32_t v) { return static_cast<double>(v); }
+};
+template <> struct Arith<int32_t> : ArithInt<int32_t> {};
+template <> struct Arith<int16_t> : ArithInt<int16_t> {};
+template <> struct Arith<int8_t> : ArithInt<int8_t> {};
+
+template <int T> __device__ __forceinline__ void team_sync(int team) {
+    if constexpr (T == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(32 * T) : "memory");
+    }
+}
+
+__device__ __forceinline__ void named_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ uint4 ld_nc_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void set_status(int32_t *status, int code) { atomicCAS(status, 0, code); }
+
+// Add s * (one 16-byte chunk of a Q row) into fields.  QT elements -> HT.
+template <typename QT, typename HT>
+__device__ __forceinline__ void add_chunk(HT *h, const uint4 &v, bool up) {
+    constexpr int VE = 16 / static_cast<int>(sizeof(QT));
+    QT q[VE];
+    *reinterpret_cast<uint4 *>(q) = v;
+    if constexpr (std::is_same<HT, float>::value) {
+        float4 *hp = reinterpret_cast<float4 *>(h);
+        float4 a = hp[0];
+        if (up) {
+            a.x = __fadd_rn(a.x, q[0]); a.y = __fadd_rn(a.y, q[1]);
+            a.z = __fadd_rn(a.z, q[2]); a.w = __fadd_rn(a.w, q[3]);
+        } else {
+            a.x = __fsub_rn(a.x, q[0]); a.y = __fsub_rn(a.y, q[1]);
+            a.z = __fsub_rn(a.z, q[2]); a.w = __fsub_rn(a.w, q[3]);
+        }
+        hp[0] = a;
+    } else {
+        static_assert(std::is_same<HT, int32_t>::value, "dense integer fields are int32");
+        int4 *hp = reinterpret_cast<int4 *>(h);
+#pragma unroll
+        for (int g = 0; g < VE / 4; ++g) {
+            int4 a = hp[g];
+            const int32_t s0 = q[4 * g + 0], s1 = q[4 * g + 1], s2 = q[4 * g + 2], s3 = q[4 * g + 3];
+            if (up) { a.x += s0; a.y += s1; a.z += s2; a.w += s3; }
+            else    { a.x -= s0; a.y -= s1; a.z -= s2; a.w -= s3; }
+            hp[g] = a;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.
+// ---------------------------------------------------------------------------
+template <typename QT, typename HT, int T, bool CSR>
+__global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const KParams P) {
+    using A = Arith<HT>;
+    using D = typename A::D;
+    using CT = typename A::C;
+    constexpr int TT = 32 * T;  // threads per team
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CtaDesc cd = P.cta[blockIdx.x];
+    const int team = threadIdx.x / TT;
+    if (team >= cd.count) return;  // idle warps take part in no barrier
+    const int tid = threadIdx.x - team * TT;
+    const int lane = threadIdx.x & 31;
+    const int wit = tid >> 5;
+    const int cid = P.cta_chains[cd.first + team];
+    const ChainDesc chd = P.chain[cid];
+    const InstDesc in = P.inst[chd.inst];
+    const int n = in.n;
+    const int ld = in.ld;
+    const int variant = P.variant;
+    const bool use_list = needs_list(variant, P.subset);
+    const int k = (variant == VAR_RF) ? n : (variant == VAR_METROPOLIS ? 1 : in.k);
+
+    const ChainSmem L = chain_smem(ld, k, static_cast<int32_t>(sizeof(HT)), use_list);
+    unsigned char *base = smem + chd.smem_off;
+    HT *h = reinterpret_cast<HT *>(base + L.fields);
+    uint32_t *xw = reinterpret_cast<uint32_t *>(base + L.xw);
+    int32_t *list = reinterpret_cast<int32_t *>(base + L.list);
+    uint32_t *bitmap = reinterpret_cast<uint32_t *>(base + L.bitmap);
+    uint32_t *red = reinterpret_cast<uint32_t *>(base + L.scratch);  // [5][32]
+    double *pub_E = reinterpret_cast<double *>(base + L.scratch + 640);
+    int32_t *pub_b = reinterpret_cast<int32_t *>(base + L.scratch + 648);
+    int32_t *swap_cnt = reinterpret_cast<int32_t *>(base + L.scratch + 652);
+    int32_t *dead_slot = reinterpret_cast<int32_t *>(base + L.scratch + 656);
+
+    const CT *bvec = reinterpret_cast<const CT *>(in.b);
+    const CT *dvec = reinterpret_cast<const CT *>(in.diag);
+
+    // ---- load the chain ----------------------------------------------------
+    {
+        const HT *gh = reinterpret_cast<const HT *>(P.fields) + static_cast<int64_t>(cid) * P.LD;
+        const uint32_t *gx = P.xbits + static_cast<int64_t>(cid) * P.W;
+        const int hchunks = ld * static_cast<int>(sizeof(HT)) / 16;
+        for (int c = tid; c < hchunks; c += TT)
+            reinterpret_cast<uint4 *>(h)[c] = reinterpret_cast<const uint4 *>(gh)[c];
+        for (int w = tid; w < ld / 32; w += TT) xw[w] = gx[w];
+    }
+    if (tid == 0) {
+        *swap_cnt = 0;
+        *dead_slot = 0;
+    }
+    ChainState st = P.state[cid];
+    float beta = in.betas[st.beta_idx];
+    const uint64_t seed = P.seed;
+    const uint32_t chain_id = static_cast<uint32_t>(cid);
+    int dead = 0;
+    bool list_valid = false;
+    int64_t tape_pos = 0;
+    team_sync<T>(team);
+
+    // Draw the random subset for stream step `sstep` into `list` (warp 0 of
+    // the team).  The set is the first k distinct values of
+    // v_m = floor(word_m n / 2^32), m = 0, 1, ...
+    auto draw_subset = [&](uint64_t sstep) {
+        if (wit == 0) {
+            for (int w = lane; w < ld / 32; w += 32) bitmap[w] = 0u;
+            __syncwarp();
+            const uint32_t cap = 64u * static_cast<uint32_t>(n) + 1024u;
+            int got = 0;
+            uint32_t m0 = 0;
+            while (got < k) {
+                const uint32_t m = m0 + lane;
+                const bool valid = m < cap;
+                const uint32_t word = rng_word(seed, TAG_SUBSET, chain_id, sstep, m);
+                const uint32_t v = __umulhi(word, static_cast<uint32_t>(n));
+                const uint32_t eq = __match_any_sync(0xFFFFFFFFu, valid ? v : 0xFFFFFFFFu);
+                const bool first = (__ffs(eq) - 1) == lane;
+                const bool seen = (bitmap[v >> 5] >> (v & 31u)) & 1u;
+                const bool acc = valid && first && !seen;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, acc);
+                const int rank = got + __popc(bal & ((1u << lane) - 1u));
+                if (acc && rank < k) list[rank] = static_cast<int32_t>(v);
+                if (acc) atomicOr(&bitmap[v >> 5], 1u << (v & 31u));
+                got += __popc(bal);
+                m0 += 32;
+                __syncwarp();
+                if (got < k && m0 >= cap) {
+                    if (lane == 0) set_status(P.status, ST_TIMEOUT);
+                    dead = 1;
+                    break;
+                }
+            }
+            if (lane == 0) *dead_slot = dead;
+        }
+        team_sync<T>(team);
+        if constexpr (T > 1) dead = *dead_slot;
+    };
+
+    // Candidate bit of position t.
+    auto cand = [&](int t) -> int {
+        if (variant == VAR_RF) return t;
+        if (use_list) return list[t];
+        int c = st.set_start + t;
+        return c >= n ? c - n : c;
+    };
+
+    auto delta_of = [&](int i) -> D {
+        const bool xi = (xw[i >> 5] >> (i & 31)) & 1u;
+        return A::delta(h[i], bvec[i], dvec[i], xi);
+    };
+
+    // Apply the move to bit j (all team threads), then flip x_j.
+    auto apply_move = [&](int j) {
+        const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
+        if constexpr (CSR) {
+            const int e0 = in.row_ptr[j], e1 = in.row_ptr[j + 1];
+            const QT *vals = reinterpret_cast<const QT *>(in.q);
+            for (int e = e0 + tid; e < e1; e += TT) {
+                const int r = in.col[e];
+                const QT qv = vals[e];
+                if constexpr (std::is_same<HT, float>::value) {
+                    h[r] = up ? __fadd_rn(h[r], qv) : __fsub_rn(h[r], qv);
+                } else {
+                    h[r] = static_cast<HT>(up ? static_cast<int32_t>(h[r]) + static_cast<int32_t>(qv)
+                                              : static_cast<int32_t>(h[r]) - static_cast<int32_t>(qv));
+                }
+            }
+            if (tid == TT - 1) {
+                const CT dv = dvec[j];
+                if constexpr (std::is_same<HT, float>::value) {
+                    h[j] = up ? __fadd_rn(h[j], dv) : __fsub_rn(h[j], dv);
+                } else {
+                    h[j] = static_cast<HT>(up ? static_cast<int32_t>(h[j]) + dv : static_cast<int32_t>(h[j]) - dv);
+                }
+            }
+        } else {
+            constexpr int VE = 16 / static_cast<int>(sizeof(QT));
+            const QT *row = reinterpret_cast<const QT *>(in.q) + static_cast<int64_t>(j) * ld;
+            const int chunks = ld / VE;
+            int c = tid;
+            // four independent 16-byte loads in flight per thread
+            for (; c + 3 * TT < chunks; c += 4 * TT) {
+                const uint4 v0 = ld_nc_v4(row + (c + 0 * TT) * VE);
+                const uint4 v1 = ld_nc_v4(row + (c + 1 * TT) * VE);
+                const uint4 v2 = ld_nc_v4(row + (c + 2 * TT) * VE);
+                const uint4 v3 = ld_nc_v4(row + (c + 3 * TT) * VE);
+                add_chunk<QT, HT>(h + (c + 0 * TT) * VE, v0, up);
+                add_chunk<QT, HT>(h + (c + 1 * TT) * VE, v1, up);
+                add_chunk<QT, HT>(h + (c + 2 * TT) * VE, v2, up);
+                add_chunk<QT, HT>(h + (c + 3 * TT) * VE, v3, up);
+            }
+            for (; c < chunks; c += TT) {
+                const uint4 v0 = ld_nc_v4(row + c * VE);
+                add_chunk<QT, HT>(h + c * VE, v0, up);
+            }
+        }
+        team_sync<T>(team);  // every thread has read x_j
+        if (tid == 0) xw[j >> 5] ^= 1u << (j & 31);
+    };
+
+    auto write_record = [&](int32_t flip, double m) {
+        if (tid == 0 && P.tape && tape_pos < P.tape_cap) {
+            const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos;
+            P.tape_flip[o] = flip;
+            P.tape_m[o] = m;
+        }
+        tape_pos += 1;
+    };
+
+    // One record.  Returns true when the record was an Unbiased period end.
+    auto one_record = [&]() -> bool {
+        const uint64_t step = static_cast<uint64_t>(st.step);
+        bool period_end = false;
+        if (variant == VAR_METROPOLIS) {
+            const uint4 wv = rng_block(seed, TAG_STEP, chain_id, step, 0);
+            const int i = static_cast<int>(__umulhi(wv.z, static_cast<uint32_t>(n)));
+            const D d = delta_of(i);
+            const float lu = det_logf(u01_grid(wv.w));
+            const float y = -__fmul_rn(beta, A::tof(d));
+            team_sync<T>(team);  // all reads of h / x done before the move
+            if (lu < y) {
+                apply_move(i);
+                st.E = __dadd_rn(st.E, A::tod(d));
+                st.flips += 1;
+                write_record(i, 1.0);
+            } else {
+                st.stays += 1;
+                write_record(-1, 1.0);
+            }
+            st.sum_m = __dadd_rn(st.sum_m, 1.0);
+        } else {
+            if (variant == VAR_BASIC) {
+                draw_subset(step);
+            } else if (use_list && !list_valid) {
+                draw_subset(static_cast<uint64_t>(st.period_start));
+                list_valid = true;
+            }
+            if (dead) return true;
+            // a2 + a3: anchor
+            uint32_t lmin = 0xFFFFFFFFu;
+            for (int t = tid; t < k; t += TT) {
+                const uint32_t kd = A::key(A::pos(delta_of(cand(t))));
+                lmin = kd < lmin ? kd : lmin;
+            }
+            uint32_t amin_k = __reduce_min_sync(0xFFFFFFFFu, lmin);
+            if constexpr (T > 1) {
+                if (lane == 0) red[0 * 32 + wit] = amin_k;
+                team_sync<T>(team);
+                amin_k = red[0];
+#pragma unroll 4
+                for (int w = 1; w < T; ++w) amin_k = red[w] < amin_k ? red[w] : amin_k;
+            }
+            const D amin = A::unkey(amin_k);
+            // a4: weights, race, quantised sum
+            uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
+            for (int t = tid; t < k; t += TT) {
+                const D dp = A::pos(delta_of(cand(t)));
+                const float w = det_expf(-__fmul_rn(beta, A::diff(dp, amin)));
+                const uint64_t qw = __float2ull_rz(__fmul_rn(w, 0x1p32f));
+                sa += static_cast<uint32_t>(qw >> 16);
+                sb += static_cast<uint32_t>(qw & 0xFFFFull);
+                const uint32_t word = rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t));
+                const float ex = det_neg_log1m(u01_fine(word));
+                const uint32_t kb = __float_as_uint(__fdiv_rn(ex, w));
+                if (kb < bkey) {  // t ascending: the first minimum is kept
+                    bkey = kb;
+                    bpos = static_cast<uint32_t>(t);
+                }
+            }
+            uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
+            uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
+            uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa);
+            uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
+            uint64_t S;
+            if constexpr (T > 1) {
+                if (lane == 0) {
+                    red[1 * 32 + wit] = wkey;
+                    red[2 * 32 + wit] = wpos;
+                    red[3 * 32 + wit] = SA;
+                    red[4 * 32 + wit] = SB;
+                }
+                team_sync<T>(team);
+                wkey = red[32];
+                wpos = red[64];
+                uint64_t SA64 = red[96], SB64 = red[128];
+                for (int w = 1; w < T; ++w) {
+                    const uint32_t kk = red[32 + w], pp = red[64 + w];
+                    if (kk < wkey || (kk == wkey && pp < wpos)) {
+                        wkey = kk;
+                        wpos = pp;
+                    }
+                    SA64 += red[96 + w];
+                    SB64 += red[128 + w];
+                }
+                S = (SA64 << 16) + SB64;
+            } else {
+                S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
+            }
+            // a5: multiplicity and budget
+            const uint4 wv = rng_block(seed, TAG_STEP, chain_id, step, 0);
+            float p;
+            int sat;
+            double m = multiplicity(S, k, beta, A::tof(amin), wv.x, wv.y, &p, &sat);
+            const int j = cand(static_cast<int>(wpos));
+            const D dj = delta_of(j);
+            team_sync<T>(team);  // reads of h, x, list done
+            bool move = true;
+            if (variant == VAR_UNBIASED) {
+                if (m <= static_cast<double>(st.L)) {
+                    st.L -= static_cast<int64_t>(m);
+                } else {
+                    move = false;
+                    m = static_cast<double>(st.L);
+                    st.L = P.L0;
+                    st.stays += 1;
+                    int ns = st.set_start + k;
+                    while (ns >= n) ns -= n;
+                    st.set_start = ns;
+                    st.period_start = static_cast<int64_t>(step) + 1;
+                    list_valid = false;
+                    period_end = true;
+                }
+            }
+            if (move) {
+                if (sat) st.saturated += 1;
+                apply_move(j);
+                st.E = __dadd_rn(st.E, A::tod(dj));
+                st.flips += 1;
+                write_record(j, m);
+            } else {
+                write_record(-1, m);
+            }
+            st.sum_m = __dadd_rn(st.sum_m, m);
+        }
+        if (st.E < st.best_E) st.best_E = st.E;
+        st.step += 1;
+        team_sync<T>(team);
+        return period_end;
+    };
+
+    // ---- main loop -----------------------------------------------------------
+    if (!P.pt) {
+        for (int64_t r = 0; r < P.steps && !dead; ++r) one_record();
+    } else {
+        const int R = P.R;
+        const int gbar = (T == 1 ? 1 : 1 + cd.count) + team / R;  // named barrier of the group
+        const int gthreads = R * TT;
+        const int64_t rounds = P.steps / P.swap_interval;
+        const int64_t per_round = variant == VAR_UNBIASED ? P.swap_interval / P.L0 : P.swap_interval;
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            if (variant == VAR_UNBIASED) {
+                int64_t periods = 0;
+                while (periods < per_round) {
+                    if (dead) { periods = per_round; break; }
+                    if (one_record()) periods += 1;
+                }
+            } else {
+                for (int64_t r = 0; r < per_round && !dead; ++r) one_record();
+            }
+            if (tid == 0) {
+                *pub_E = st.E;
+                *pub_b = st.beta_idx;
+            }
+            named_sync(gbar, gthreads);
+            if (chd.slot == 0 && tid == 0) {
+                // exchange round for this group; slots of the group are the R
+                // consecutive teams starting at this one
+                const uint64_t done = static_cast<uint64_t>(st.sum_m) / static_cast<uint64_t>(P.swap_interval);
+                const uint64_t rnd = done - 1;
+                const ChainDesc *cds = P.chain;
+                int slot_of[32];
+                for (int s = 0; s < R; ++s) {
+                    const int oc = P.cta_chains[cd.first + team + s];
+                    const unsigned char *ob = smem + cds[oc].smem_off;
+                    slot_of[*reinterpret_cast<const int32_t *>(ob + L.scratch + 648)] = s;
+                }
+                int q = 0;
+                for (int a = static_cast<int>(rnd & 1u); a + 1 < R; a += 2, ++q) {
+                    const int sa_ = slot_of[a], sb_ = slot_of[a + 1];
+                    const int ca = P.cta_chains[cd.first + team + sa_];
+                    const int cb = P.cta_chains[cd.first + team + sb_];
+                    unsigned char *pa = smem + cds[ca].smem_off + L.scratch;
+                    unsigned char *pb = smem + cds[cb].smem_off + L.scratch;
+                    const double Ea = *reinterpret_cast<double *>(pa + 640);
+                    const double Eb = *reinterpret_cast<double *>(pb + 640);
+                    const float db = __fsub_rn(in.betas[a], in.betas[a + 1]);
+                    const float de = __double2float_rn(__dsub_rn(Ea, Eb));
+                    const float xr = __fmul_rn(db, de);
+                    const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd.group), rnd,
+                                                static_cast<uint32_t>(q));
+                    if (det_logf(u01_grid(w)) < xr) {
+                        *reinterpret_cast<int32_t *>(pa + 648) = a + 1;
+                        *reinterpret_cast<int32_t *>(pb + 648) = a;
+                        slot_of[a] = sb_;
+                        slot_of[a + 1] = sa_;
+                        // count on both chains' published slot: use the high bit area
+                        atomicAdd(reinterpret_cast<int32_t *>(pa + 652), 1);
+                        atomicAdd(reinterpret_cast<int32_t *>(pb + 652), 1);
+                    }
+                }
+            }
+            named_sync(gbar, gthreads);
+            st.beta_idx = *pub_b;
+            st.swaps += *swap_cnt;
+            team_sync<T>(team);
+            if (tid == 0) *swap_cnt = 0;
+            beta = in.betas[st.beta_idx];
+            team_sync<T>(team);
+        }
+    }
+
+    // ---- write the chain back ------------------------------------------------
+    team_sync<T>(team);
+    {
+        HT *gh = reinterpret_cast<HT *>(P.fields) + static_cast<int64_t>(cid) * P.LD;
+        uint32_t *gx = P.xbits + static_cast<int64_t>(cid) * P.W;
+        const int hchunks = ld * static_cast<int>(sizeof(HT)) / 16;
+        for (int c = tid; c < hchunks; c += TT)
+            reinterpret_cast<uint4 *>(gh)[c] = reinterpret_cast<const uint4 *>(h)[c];
+        for (int w = tid; w < ld / 32; w += TT) gx[w] = xw[w];
+    }
+    if (tid == 0) {
+        st.tape_records = tape_pos < P.tape_cap ? tape_pos : P.tape_cap;
+        if (!P.tape) st.tape_records = 0;
+        P.state[cid] = st;
+    }
+}
+
+}  // namespace pnsk

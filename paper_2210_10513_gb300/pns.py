@@ -1,0 +1,292 @@
+"""Thin ctypes binding of libpns (include/pns.h).
+
+Argument marshalling only: every step of the sampler runs in the CUDA
+library.  The functions keep the C names (pns_create, pns_run, pns_read,
+pns_fields, pns_get_info, pns_checkpoint, pns_restore, pns_destroy,
+pns_last_error).  Arrays may be numpy arrays (host memory) or torch tensors
+(host or device); streams are torch streams or raw cudaStream_t integers.
+If the library is missing this module raises: there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpns.so")
+
+BASIC, UNBIASED, RF, METROPOLIS = 0, 1, 2, 3
+VARIANTS = {"basic": BASIC, "unbiased": UNBIASED, "rf": RF, "metropolis": METROPOLIS}
+Q_I16, Q_I32, Q_F32 = 0, 1, 2
+DENSE, CSR = 0, 1
+SYSTEMATIC, RANDOM = 0, 1
+
+STATUS = {0: "PNS_OK", 1: "PNS_ERR_INVALID_ARG", 2: "PNS_ERR_NOT_SYMMETRIC", 3: "PNS_ERR_RANGE", 4: "PNS_ERR_OOM",
+          5: "PNS_ERR_CUDA", 6: "PNS_ERR_TIMEOUT", 7: "PNS_ERR_STATE", 8: "PNS_ERR_UNSUPPORTED"}
+
+
+class PnsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+class pns_problem(C.Structure):
+    _fields_ = [("n", C.c_int32), ("fmt", C.c_int32), ("qtype", C.c_int32), ("n_replicas", C.c_int32),
+                ("k", C.c_int32), ("reserved", C.c_int32), ("q", C.c_void_p), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("nnz", C.c_int64),
+                ("diag", C.c_void_p), ("b", C.c_void_p), ("betas", C.c_void_p)]
+
+
+class pns_config(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("k", C.c_int32), ("subset", C.c_int32), ("chains_per_replica", C.c_int32),
+                ("L0", C.c_int64), ("swap_interval", C.c_int64), ("seed", C.c_uint64), ("tape", C.c_int32),
+                ("warps_per_chain", C.c_int32), ("x0", C.c_void_p)]
+
+
+class pns_info(C.Structure):
+    _fields_ = [("chains", C.c_int64), ("words_per_chain", C.c_int32), ("field_stride", C.c_int32),
+                ("field_bytes", C.c_int32), ("field_is_float", C.c_int32), ("tape_capacity", C.c_int64),
+                ("warps_per_chain", C.c_int32), ("ctas", C.c_int32)]
+
+
+class pns_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("flips", C.c_int64), ("stays", C.c_int64), ("saturated", C.c_int64),
+                ("swaps_accepted", C.c_int64), ("budget_left", C.c_int64), ("tape_records", C.c_int64),
+                ("set_start", C.c_int32), ("beta_idx", C.c_int32), ("energy", C.c_double), ("sum_m", C.c_double),
+                ("best_energy", C.c_double)]
+
+
+STATS_DTYPE = np.dtype([("steps", np.int64), ("flips", np.int64), ("stays", np.int64), ("saturated", np.int64),
+                        ("swaps_accepted", np.int64), ("budget_left", np.int64), ("tape_records", np.int64),
+                        ("set_start", np.int32), ("beta_idx", np.int32), ("energy", np.float64),
+                        ("sum_m", np.float64), ("best_energy", np.float64)])
+assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
+
+EXPORTS = ("pns_create", "pns_run", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore",
+           "pns_destroy", "pns_last_error")
+
+_lib = None
+
+
+def lib():
+    """Load libpns.so (built by paper_2210_10513_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpns.so is not built (run paper_2210_10513_gb300.build.build()); "
+                               "the sampler has no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.pns_create.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(vp)]
+        L.pns_run.argtypes = [vp, C.c_int64, vp]
+        L.pns_read.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.pns_fields.argtypes = [vp, vp, vp]
+        L.pns_get_info.argtypes = [vp, vp]
+        L.pns_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.pns_restore.argtypes = [vp, vp, C.c_size_t]
+        L.pns_destroy.argtypes = [vp]
+        L.pns_destroy.restype = None
+        L.pns_last_error.argtypes = []
+        L.pns_last_error.restype = C.c_char_p
+        for name in ("pns_create", "pns_run", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint",
+                     "pns_restore"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def pns_last_error():
+    return lib().pns_last_error().decode()
+
+
+def _check(status):
+    if status != 0:
+        raise PnsError(status, pns_last_error())
+
+
+def _addr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _qtype_of(dtype):
+    dt = np.dtype(str(dtype).replace("torch.", ""))
+    if dt == np.int16:
+        return Q_I16
+    if dt == np.int32:
+        return Q_I32
+    if dt == np.float32:
+        return Q_F32
+    raise TypeError("Q must be int16, int32 or float32, got %s" % dt)
+
+
+def make_problem(n, q=None, b=None, betas=(1.0,), csr=None, k=0, keep=None):
+    """Fill a pns_problem.  `keep` collects the arrays that must stay alive
+    until pns_create returns."""
+    keep = keep if keep is not None else []
+    p = pns_problem()
+    p.n = int(n)
+    p.k = int(k)
+    betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float32).reshape(-1))
+    keep.append(betas)
+    p.betas = _addr(betas)
+    p.n_replicas = len(betas)
+    if csr is not None:
+        row_ptr, col, val, diag = csr
+        p.fmt = CSR
+        p.qtype = _qtype_of(val.dtype)
+        for a in (row_ptr, col, val, diag):
+            if a is not None:
+                keep.append(a)
+        p.row_ptr, p.col, p.q, p.diag = _addr(row_ptr), _addr(col), _addr(val), _addr(diag)
+        p.nnz = int(len(col))
+    else:
+        p.fmt = DENSE
+        p.qtype = _qtype_of(q.dtype)
+        keep.append(q)
+        p.q = _addr(q)
+    if b is not None:
+        keep.append(b)
+        p.b = _addr(b)
+    return p
+
+
+def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100, swap_interval=0, seed=0,
+                tape=False, warps_per_chain=0, x0=None):
+    c = pns_config()
+    c.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    c.k = int(k)
+    c.subset = {"systematic": SYSTEMATIC, "random": RANDOM}[subset] if isinstance(subset, str) else int(subset)
+    c.chains_per_replica = int(chains_per_replica)
+    c.L0 = int(L0)
+    c.swap_interval = int(swap_interval)
+    c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    c.tape = int(bool(tape))
+    c.warps_per_chain = int(warps_per_chain)
+    c.x0 = _addr(x0)
+    return c
+
+
+def pns_create(problems, config, stream=None):
+    arr = (pns_problem * len(problems))(*problems)
+    ctx = C.c_void_p()
+    _check(lib().pns_create(C.cast(arr, C.c_void_p), len(problems), C.byref(config), _stream(stream), C.byref(ctx)))
+    return ctx
+
+
+def pns_run(ctx, steps, stream=None):
+    _check(lib().pns_run(ctx, int(steps), _stream(stream)))
+
+
+def pns_get_info(ctx):
+    info = pns_info()
+    _check(lib().pns_get_info(ctx, C.byref(info)))
+    return info
+
+
+def pns_read(ctx, states=None, multiplicities=None, flips=None, stats=None, stream=None):
+    _check(lib().pns_read(ctx, _addr(states), _addr(multiplicities), _addr(flips), _addr(stats), _stream(stream)))
+
+
+def pns_fields(ctx, out, stream=None):
+    _check(lib().pns_fields(ctx, _addr(out), _stream(stream)))
+
+
+def pns_checkpoint(ctx):
+    n = C.c_size_t(0)
+    _check(lib().pns_checkpoint(ctx, None, C.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(lib().pns_checkpoint(ctx, _addr(buf), C.byref(n)))
+    return buf
+
+
+def pns_restore(ctx, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().pns_restore(ctx, _addr(buf), buf.nbytes))
+
+
+def pns_destroy(ctx):
+    if ctx:
+        lib().pns_destroy(ctx)
+
+
+class Sampler:
+    """Owns one pns context.  Marshals numpy / torch inputs into the C calls
+    and returns numpy results."""
+
+    def __init__(self, problems, variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100,
+                 swap_interval=0, seed=0, tape=False, warps_per_chain=0, x0=None, stream=None):
+        keep = []
+        probs = []
+        for pr in problems:
+            probs.append(make_problem(keep=keep, **pr))
+        if x0 is not None:
+            keep.append(x0)
+        cfg = make_config(variant, k, subset, chains_per_replica, L0, swap_interval, seed, tape, warps_per_chain, x0)
+        self.ctx = pns_create(probs, cfg, stream)
+        self.info = pns_get_info(self.ctx)
+        self.tape = bool(tape)
+
+    def run(self, steps, stream=None):
+        pns_run(self.ctx, steps, stream)
+
+    def read(self, stream=None, tape=True):
+        info = pns_get_info(self.ctx)
+        C_ = info.chains
+        states = np.empty((C_, info.words_per_chain), dtype=np.uint32)
+        stats = np.empty(C_, dtype=STATS_DTYPE)
+        m = f = None
+        if tape and self.tape and info.tape_capacity > 0:
+            m = np.empty((C_, info.tape_capacity), dtype=np.float64)
+            f = np.empty((C_, info.tape_capacity), dtype=np.int32)
+        pns_read(self.ctx, states, m, f, stats, stream)
+        return dict(states=states, stats=stats, m=m, flips=f)
+
+    def fields(self, stream=None):
+        info = pns_get_info(self.ctx)
+        dt = np.float32 if info.field_is_float else {1: np.int8, 2: np.int16, 4: np.int32}[info.field_bytes]
+        out = np.empty((info.chains, info.field_stride), dtype=dt)
+        pns_fields(self.ctx, out, stream)
+        return out
+
+    def checkpoint(self):
+        return pns_checkpoint(self.ctx)
+
+    def restore(self, buf):
+        pns_restore(self.ctx, buf)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pns_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

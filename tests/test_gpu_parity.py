@@ -1,0 +1,194 @@
+"""CUDA sampler vs the CPU oracle, record by record, through the C ABI.
+
+Integer QUBOs: bit-exact flip tapes, multiplicities, states, fields, energies
+and statistics.  fp32 QUBOs: the same, because both sides take every
+decision in fp32 with one operation order (the fields are then bit-equal
+too); the fp64-recomputed fields are within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_2210_10513_gb300 import synth
+from tests.gpu_helpers import assert_chain_equal, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _int_problem(n, lo=-100, hi=100, seed=0, dtype=np.int16, b=True, betas=(0.05,)):
+    return dict(n=n, q=synth.dense_int(n, lo, hi, seed, dtype),
+                b=synth.vector_int(n, lo, hi, seed, dtype) if b else None, betas=list(betas))
+
+
+def _check_all(problems, steps, chains, **cfg):
+    g = gpu_run(problems, steps, tape=True, **cfg)
+    ids = list(range(chains))
+    ref = oracle_run(problems, steps, ids, **cfg)
+    for cid in ids:
+        n = problems[ref[cid]["instance"]]["n"]
+        assert_chain_equal(g, ref[cid], cid, n, steps)
+    return g
+
+
+@pytest.mark.parametrize("variant,k,subset", [("rf", 16, "systematic"), ("basic", 4, "systematic"),
+                                              ("unbiased", 4, "systematic"), ("unbiased", 4, "random"),
+                                              ("metropolis", 1, "systematic")])
+def test_small_dense_n16(variant, k, subset):
+    p = dict(n=16, q=synth.dense_int(16, -8, 8, 0, np.int32), b=None, betas=[1.0])
+    _check_all([p], 3000, 8, variant=variant, k=k, subset=subset, chains_per_replica=8, seed=3)
+
+
+@pytest.mark.parametrize("variant", ["basic", "unbiased"])
+def test_dense_int16_n1024(variant):
+    p = _int_problem(1024)
+    _check_all([p], 1500, 6, variant=variant, k=64, chains_per_replica=6, seed=11)
+
+
+@pytest.mark.parametrize("n,k,subset", [(200, 13, "systematic"), (200, 13, "random"), (37, 37, "systematic"),
+                                        (33, 1, "systematic"), (1, 1, "systematic")])
+def test_ragged_sizes(n, k, subset):
+    p = _int_problem(n, lo=-30, hi=30, seed=n, dtype=np.int32, betas=(0.3,))
+    _check_all([p], 2000, 4, variant="unbiased", k=k, subset=subset, chains_per_replica=4, seed=5, L0=50)
+
+
+@pytest.mark.parametrize("variant,k", [("unbiased", 17), ("basic", 9), ("rf", 300), ("metropolis", 1)])
+def test_fp32_dense(variant, k):
+    n = 300
+    p = dict(n=n, q=synth.dense_normal(n, 1.0, 2), b=synth.vector_normal(n, 0.5, 2), betas=[0.7])
+    g = _check_all([p], 1500, 4, variant=variant, k=k, chains_per_replica=4, seed=2)
+    # fields against an fp64 recomputation from the final states
+    bits = synth.unpack_bits(g["states"][:4], n).astype(np.float64)
+    h64 = bits @ p["q"].astype(np.float64) + p["b"].astype(np.float64)
+    scale = np.abs(p["q"]).sum(1).max()
+    assert np.abs(g["fields"][:4, :n] - h64).max() <= 1e-5 * scale
+
+
+def test_random_initial_states_and_multiple_instances():
+    probs = [_int_problem(96, seed=1, dtype=np.int32, betas=(0.05, 0.2)),
+             _int_problem(160, seed=2, dtype=np.int32, betas=(0.1,))]
+    chains = 2 * 3 + 1 * 3
+    W = 160 // 32
+    bits = np.zeros((chains, 160), np.uint8)
+    rb = synth.random_bits(chains, 160, seed=4)
+    ns = [96] * 6 + [160] * 3
+    for c in range(chains):
+        bits[c, :ns[c]] = rb[c, :ns[c]]
+    x0 = synth.pack_bits(bits)
+    assert x0.shape == (chains, W)
+    g = gpu_run(probs, 1000, tape=True, variant="unbiased", k=8, chains_per_replica=3, seed=9, x0=x0)
+    ref = oracle_run(probs, 1000, list(range(chains)), x0=x0, variant="unbiased", k=8, chains_per_replica=3, seed=9)
+    for cid in range(chains):
+        assert_chain_equal(g, ref[cid], cid, ns[cid], 1000)
+
+
+@pytest.mark.parametrize("T", [1, 4, 8])
+def test_csr_lattice(T):
+    side = 16
+    csr = synth.lattice_csr(side, seed=3)
+    p = dict(n=side * side, csr=csr, b=None, betas=[0.44])
+    g = _check_all([p], 2000, 3, variant="unbiased", k=64, chains_per_replica=3, seed=4, warps_per_chain=T)
+    assert g["info"].field_bytes == 1  # |h| <= 6 fits int8
+
+
+def test_mapping_does_not_change_results(monkeypatch):
+    p = _int_problem(256, dtype=np.int32)
+    base = gpu_run([p], 800, tape=True, variant="unbiased", k=40, chains_per_replica=12, seed=1, warps_per_chain=1)
+    for T in (2, 4):
+        o = gpu_run([p], 800, tape=True, variant="unbiased", k=40, chains_per_replica=12, seed=1, warps_per_chain=T)
+        np.testing.assert_array_equal(o["flips"], base["flips"])
+        np.testing.assert_array_equal(o["m"], base["m"])
+        np.testing.assert_array_equal(o["fields"], base["fields"])
+    monkeypatch.setenv("PNS_CHAINS_PER_CTA", "5")
+    o = gpu_run([p], 800, tape=True, variant="unbiased", k=40, chains_per_replica=12, seed=1, warps_per_chain=1)
+    np.testing.assert_array_equal(o["flips"], base["flips"])
+    np.testing.assert_array_equal(o["m"], base["m"])
+
+
+def test_host_inputs_equal_device_inputs():
+    p = _int_problem(128, dtype=np.int16)
+    a = gpu_run([p], 500, tape=True, device_inputs=True, variant="basic", k=16, chains_per_replica=4, seed=2)
+    b = gpu_run([p], 500, tape=True, device_inputs=False, variant="basic", k=16, chains_per_replica=4, seed=2)
+    np.testing.assert_array_equal(a["flips"], b["flips"])
+    np.testing.assert_array_equal(a["m"], b["m"])
+
+
+def test_consecutive_runs_continue_the_chain():
+    p = _int_problem(64, dtype=np.int32)
+    two = gpu_run([p], 700, runs=2, tape=True, variant="unbiased", k=8, chains_per_replica=3, seed=6)
+    one = gpu_run([p], 1400, tape=True, variant="unbiased", k=8, chains_per_replica=3, seed=6)
+    first, second = two["all"]
+    np.testing.assert_array_equal(np.concatenate([first["flips"], second["flips"]], axis=1), one["flips"])
+    np.testing.assert_array_equal(np.concatenate([first["m"], second["m"]], axis=1), one["m"])
+    np.testing.assert_array_equal(two["states"], one["states"])
+
+
+def test_checkpoint_restore_bit_identical():
+    from paper_2210_10513_gb300 import pns
+    from tests.gpu_helpers import to_dev
+    p = dict(n=100, q=synth.dense_normal(100, 1.0, 8), b=synth.vector_normal(100, 1.0, 8), betas=[0.5])
+    s = pns.Sampler([dict(n=100, q=to_dev(p["q"]), b=to_dev(p["b"]), betas=[0.5])], variant="unbiased", k=10,
+                    subset="random", chains_per_replica=4, seed=3, tape=True)
+    s.run(500)
+    ck = s.checkpoint()
+    s.run(600)
+    a = s.read()
+    fa = s.fields()
+    s.restore(ck)
+    s.run(600)
+    b = s.read()
+    fb = s.fields()
+    s.close()
+    np.testing.assert_array_equal(a["flips"], b["flips"])
+    np.testing.assert_array_equal(a["m"], b["m"])
+    np.testing.assert_array_equal(a["states"], b["states"])
+    np.testing.assert_array_equal(fa, fb)
+    np.testing.assert_array_equal(a["stats"], b["stats"])
+
+
+def test_rf_equals_unbiased_full_set():
+    p = _int_problem(48, dtype=np.int32, betas=(0.2,))
+    a = gpu_run([p], 1000, tape=True, variant="rf", chains_per_replica=2, seed=5)
+    b = gpu_run([p], 1000, tape=True, variant="unbiased", k=48, L0=2**62, chains_per_replica=2, seed=5)
+    np.testing.assert_array_equal(a["flips"], b["flips"])
+    np.testing.assert_array_equal(a["m"], b["m"])
+
+
+def test_beta_zero_and_budget_one():
+    p = _int_problem(40, dtype=np.int32, betas=(0.0,))
+    _check_all([p], 500, 2, variant="unbiased", k=5, L0=1, chains_per_replica=2, seed=8)
+    _check_all([p], 500, 2, variant="basic", k=40, chains_per_replica=2, seed=8)
+
+
+@pytest.mark.parametrize("bad", ["asym", "nan", "range", "k", "csr_mirror"])
+def test_invalid_inputs_rejected(bad):
+    from paper_2210_10513_gb300 import pns
+    n = 8
+    q = synth.dense_int(n, -3, 3, 0, np.int32)
+    kw = dict(variant="unbiased", k=2)
+    prob = dict(n=n, q=q, betas=[1.0])
+    expect = pns.PnsError
+    if bad == "asym":
+        q = q.copy()
+        q[0, 1] += 1
+        prob["q"] = q
+        status = 2
+    elif bad == "nan":
+        qf = synth.dense_normal(n, 1.0, 0)
+        qf[2, 2] = np.nan
+        prob["q"] = qf
+        status = 3
+    elif bad == "range":
+        q = np.full((n, n), 2**28, dtype=np.int32)
+        prob["q"] = q
+        status = 3
+    elif bad == "k":
+        kw["k"] = n + 1
+        status = 1
+    else:
+        row_ptr, col, val, diag = synth.lattice_csr(4, seed=1)
+        val = val.copy()
+        val[0] = -val[0] if val[0] != 0 else 1
+        prob = dict(n=16, csr=(row_ptr, col, val, diag), betas=[1.0])
+        status = 2
+    with pytest.raises(expect) as ei:
+        pns.Sampler([prob], **kw)
+    assert ei.value.status == status

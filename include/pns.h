@@ -100,6 +100,9 @@ typedef struct {
     uint64_t seed;             /* Philox key */
     int32_t tape;              /* 0: no per-step records; 1: record (flip, M) every step */
     int32_t warps_per_chain;   /* 0: choose automatically; else 1, 2, 4, 8, 16 or 32 */
+    int32_t chains_per_cta;    /* 0: choose automatically; else at most this many chains
+                                  (or exchange groups) per CTA */
+    int32_t reserved;          /* must be 0 */
     const uint32_t *x0;        /* NULL (all zeros) or initial bit-packed states: chain c,
                                   bit i at word c*W + i/32, bit i%32; W = pns_info.words_per_chain */
 } pns_config;
@@ -148,6 +151,11 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
  * Asynchronous on `stream`; returns launch errors only.  With cfg.tape = 1 the
  * records of this run replace the tape. */
 pns_status pns_run(pns_ctx *ctx, int64_t steps, void *stream);
+
+/* The plain form of pns_run: the same records, but each CTA of the plan is
+ * its own launch, one after another on `stream` (with chains_per_cta = 1,
+ * one chain per launch).  Exists to measure what batching buys. */
+pns_status pns_run_plain(pns_ctx *ctx, int64_t steps, void *stream);
 
 /* Synchronises `stream` and copies out: states (chains x W words), the tape
  * (chains x tape_capacity M values and flip indices, -1 = stay; entries past a

@@ -58,7 +58,7 @@ constexpr uint64_t kCkptMagic = 0x31504b4353504e50ull;  // "PNSCKP1"
 struct pns_ctx {
     int device = 0;
     pns_config cfg{};
-    int fmt = 0, qtype = 0, is_float = 0, hbytes = 4, T = 1;
+    int fmt = 0, qtype = 0, is_float = 0, hbytes = 4, T = 1, prod = 0;
     std::vector<InstHost> inst;
     int32_t max_ld = 32, LD = 32, W = 1;
     int64_t chains = 0;
@@ -112,6 +112,8 @@ pns_status check_args(const pns_problem *probs, int32_t n_probs, const pns_confi
     if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32))
         return fail(PNS_ERR_INVALID_ARG, "warps_per_chain must be 0, 1, 2, 4, 8, 16 or 32");
     if (cfg->swap_interval < 0) return fail(PNS_ERR_INVALID_ARG, "swap_interval must be >= 0");
+    if (cfg->chains_per_cta < 0 || cfg->reserved != 0)
+        return fail(PNS_ERR_INVALID_ARG, "chains_per_cta must be >= 0 and reserved 0");
     if (cfg->swap_interval > 0) {
         if (cfg->variant != PNS_UNBIASED && cfg->variant != PNS_METROPOLIS)
             return fail(PNS_ERR_INVALID_ARG, "replica exchange needs PNS_UNBIASED or PNS_METROPOLIS");
@@ -171,8 +173,13 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
                        int per_cta_override, PlanOut &out) {
     const int T = c.T;
     const bool list = needs_list(c.cfg.variant, c.cfg.subset);
+    const bool slot_list = c.prod > 0 && c.cfg.variant == PNS_BASIC;
     const bool pt = c.cfg.swap_interval > 0;
-    const int teams_cap = T == 32 ? 1 : std::min(512 / (32 * T), T > 1 ? 15 : 16);
+    const int TT = 32 * (T + c.prod);
+    // named barriers per CTA (ids 1..15): two per team when a team has more
+    // than one warp, then one per exchange group
+    const bool team_bars = TT > 32;
+    const int teams_cap = T == 32 ? 1 : std::min(512 / TT, team_bars ? 7 : 16);
     struct Unit {
         int32_t first, count, bytes;
     };
@@ -180,7 +187,7 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     const int R = pt ? c.R : 1;
     for (int64_t i = 0; i < c.chains; i += R) {
         const InstHost &ih = c.inst[chains[i].inst];
-        const int32_t per = chain_smem(ih.ld, ih.k, c.hbytes, list).total;
+        const int32_t per = chain_smem(ih.ld, ih.k, c.hbytes, list, c.prod > 0, slot_list).total;
         units.push_back({static_cast<int32_t>(i), R, per * R});
     }
     if (R > teams_cap) return fail(PNS_ERR_UNSUPPORTED, "exchange group of %d chains exceeds %d teams per CTA", R, teams_cap);
@@ -208,7 +215,7 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
             return fail(PNS_ERR_UNSUPPORTED, "a chain (or exchange group) needs %d bytes of shared memory, over %zu",
                         u.bytes, smem_cap);
         // named barriers: ids 1..teams for T > 1 teams, then one per exchange group; 15 at most
-        const bool bars_ok = !pt || (T == 1 ? cur_groups + 1 <= 15 : cur_teams + u.count + cur_groups + 1 <= 15);
+        const bool bars_ok = !pt || (team_bars ? 2 * (cur_teams + u.count) + cur_groups + 1 <= 15 : cur_groups + 1 <= 15);
         const bool fits = cur_teams + u.count <= teams_cap && cur_bytes + u.bytes <= smem_cap && cur_units < target &&
                           bars_ok;
         if (!fits) close();
@@ -225,10 +232,10 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     close();
     int max_teams = 0;
     for (const CtaDesc &d : out.cta) max_teams = std::max(max_teams, static_cast<int>(d.count));
-    out.block = max_teams * 32 * T;
-    if (pt && T == 1) {
-        for (const CtaDesc &d : out.cta)
-            if (d.groups > 15) return fail(PNS_ERR_UNSUPPORTED, "too many exchange groups in one CTA");
+    out.block = max_teams * TT;
+    for (const CtaDesc &d : out.cta) {
+        const int ids = (team_bars ? 2 * d.count : 0) + (pt ? d.groups : 0);
+        if (ids > 15) return fail(PNS_ERR_UNSUPPORTED, "a CTA needs %d named barriers (15 available)", ids);
     }
     return PNS_OK;
 }
@@ -474,9 +481,18 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
             return fail(PNS_ERR_UNSUPPORTED, "warps_per_chain = %d is not built for this format", c->T);
         c->T = 1;
     }
+    // A producer warp per chain pays off when the GPU is latency-bound (few
+    // warps per SM); with many chains every warp already has work.
+    c->prod = 0;
+    if (c->T < 32) {
+        const int64_t warps = c->chains * c->T;
+        c->prod = warps <= 8ll * num_sms ? 1 : 0;
+    }
+    if (const char *e = getenv("PNS_PRODUCER_WARPS")) c->prod = atoi(e) > 0 && c->T < 32 ? 1 : 0;
     PlanOut pl;
-    int per_cta = 0;
-    if (const char *e = getenv("PNS_CHAINS_PER_CTA")) per_cta = atoi(e);
+    int per_cta = cfg->chains_per_cta;
+    if (per_cta == 0)
+        if (const char *e = getenv("PNS_CHAINS_PER_CTA")) per_cta = atoi(e);
     st = plan(*c, chains, num_sms, static_cast<size_t>(smem_optin), per_cta, pl);
     if (st != PNS_OK) return st;
     for (int64_t i = 0; i < c->chains; ++i) chains[i].smem_off = pl.smem_off[i];
@@ -528,7 +544,7 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     return PNS_OK;
 }
 
-pns_status pns_run(pns_ctx *c, int64_t steps, void *stream) {
+static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) {
     if (!c) return fail(PNS_ERR_INVALID_ARG, "ctx is NULL");
     if (c->latched) return fail(PNS_ERR_STATE, "context holds a device error (%d); restore or destroy", c->latched);
     if (steps < 0) return fail(PNS_ERR_INVALID_ARG, "steps must be >= 0");
@@ -580,9 +596,21 @@ pns_status pns_run(pns_ctx *c, int64_t steps, void *stream) {
     P.R = pt ? c->R : 1;
     P.pt = pt ? 1 : 0;
     P.tape = c->cfg.tape;
-    CU(launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, P, c->n_cta, c->block, c->smem, s));
+    P.prod = c->prod;
+    if (!plain) {
+        CU(launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, P, c->n_cta, c->block, c->smem, s));
+    } else {
+        for (int b = 0; b < c->n_cta; ++b) {
+            P.cta = c->d_cta + b;
+            CU(launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, P, 1, c->block, c->smem, s));
+        }
+    }
     return PNS_OK;
 }
+
+pns_status pns_run(pns_ctx *c, int64_t steps, void *stream) { return run_impl(c, steps, stream, false); }
+
+pns_status pns_run_plain(pns_ctx *c, int64_t steps, void *stream) { return run_impl(c, steps, stream, true); }
 
 static pns_status sync_and_check(pns_ctx *c, cudaStream_t s) {
     CU(cudaStreamSynchronize(s));

@@ -81,25 +81,31 @@ struct KParams {
     int32_t R;              // chains per exchange group (1 without exchange)
     int32_t pt;             // exchange on
     int32_t tape;
-    int32_t pad;
+    int32_t prod;           // producer warps per chain (0: consumers draw their own numbers)
 };
 
 PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }
 
 // Byte layout of one chain's shared-memory area.  Both the planner and the
-// kernel derive it from (ld, k, field bytes, whether a subset list is kept).
+// kernel derive it from (ld, k, field bytes, whether a subset list is kept,
+// whether a producer warp fills the two look-ahead slots).  A slot holds the
+// state-independent draws of one record: 16 bytes of scalars (the
+// multiplicity's Exp(1), the Metropolis index and log-uniform, a dead flag),
+// the k race exponentials and, for Basic PNS, the record's k-subset.
 struct ChainSmem {
-    int32_t fields, xw, list, bitmap, scratch, total;
+    int32_t fields, xw, list, bitmap, slots, slot_bytes, scratch, total;
 };
 
-PNS_HD ChainSmem chain_smem(int32_t ld, int32_t k, int32_t hbytes, bool list) {
+PNS_HD ChainSmem chain_smem(int32_t ld, int32_t k, int32_t hbytes, bool list, bool slots, bool slot_list) {
     ChainSmem s;
     s.fields = 0;
     s.xw = round16(ld * hbytes);
     s.list = s.xw + round16(ld / 8);
     s.bitmap = s.list + (list ? round16(k * 4) : 0);
-    s.scratch = s.bitmap + (list ? round16(ld / 8) : 0);
-    s.total = s.scratch + 768;   // 5 partials x 32 warps x 4 B, then the exchange publish slot
+    s.slots = s.bitmap + (list ? round16(ld / 8) : 0);
+    s.slot_bytes = slots ? round16(16 + 4 * k + (slot_list ? 4 * k : 0)) : 0;
+    s.scratch = s.slots + 2 * s.slot_bytes;
+    s.total = s.scratch + 768;   // 5 partials x 32 warps x 4 B, then publish / control words
     return s;
 }
 

@@ -1,10 +1,12 @@
 // pns_sampler.cuh -- the persistent batched sampling kernel.
 //
-// One "team" of T warps owns one chain for the whole launch.  The chain's
-// local fields h = Qx + b and its packed bits live in shared memory; the
-// instance's Q rows stream from HBM / L2 with 16-byte non-coherent loads.  A
-// CTA holds several teams (several chains, or the replicas of exchange
-// groups), packed by the host planner.  Per record:
+// One team of warps owns one chain for the whole launch: TC consumer warps
+// that carry the state-dependent chain of each record, and (optionally) a
+// producer warp that draws the state-independent random numbers one record
+// ahead into a double-buffered shared-memory slot.  The chain's local fields
+// h = Qx + b and its packed bits live in shared memory; Q rows stream from
+// HBM / L2 with 16-byte non-coherent loads.  A CTA holds several teams (or the
+// replicas of exchange groups), packed by the host planner.  Per record:
 //
 //   a1  candidate set N_i: systematic window, drawn k-subset, all bits (RF)
 //   a2  Delta_t = s_i (2 h_i - b_i) + Q_ii for each candidate (shared memory)
@@ -17,8 +19,9 @@
 //   a8  (exchange) at period ends all replicas of a group meet at a named
 //       barrier and adjacent temperatures swap.
 //
-// Reductions are integer (min / add) or lexicographic (key, position), so a
-// chain's records do not depend on T or on how chains are packed.
+// Reductions are integer (min / add) or lexicographic (key, position), and
+// every random number is a pure function of (seed, chain, step, position),
+// so a chain's records do not depend on the team shape or on the packing.
 #pragma once
 
 #include <cstdint>
@@ -67,14 +70,6 @@ template <> struct Arith<int32_t> : ArithInt<int32_t> {};
 template <> struct Arith<int16_t> : ArithInt<int16_t> {};
 template <> struct Arith<int8_t> : ArithInt<int8_t> {};
 
-template <int T> __device__ __forceinline__ void team_sync(int team) {
-    if constexpr (T == 1) {
-        __syncwarp();
-    } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(32 * T) : "memory");
-    }
-}
-
 __device__ __forceinline__ void named_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
@@ -120,23 +115,101 @@ __device__ __forceinline__ void add_chunk(HT *h, const uint4 &v, bool up) {
     }
 }
 
+// The race exponential of position t: -ln(1 - V), V the fine uniform of
+// Philox word t of (RACE, chain, step).
+__device__ __forceinline__ float race_exp(uint32_t word) { return det_neg_log1m(u01_fine(word)); }
+
+// Scalars of one record that do not depend on the chain state.
+struct RecordDraws {
+    float e1;      // Exp(1) of the multiplicity, from STEP words 0 and 1
+    int32_t mi;    // Metropolis proposal index (STEP word 2)
+    float mlu;     // Metropolis log-uniform (STEP word 3)
+};
+
+__device__ __forceinline__ RecordDraws record_draws(uint64_t seed, uint32_t chain, uint64_t step, int n) {
+    const uint4 w = rng_block(seed, TAG_STEP, chain, step, 0);
+    RecordDraws d;
+    d.e1 = -det_logf(u01_fine64((static_cast<uint64_t>(w.y) << 32) | static_cast<uint64_t>(w.x)));
+    d.mi = static_cast<int32_t>(__umulhi(w.z, static_cast<uint32_t>(n)));
+    d.mlu = det_logf(u01_grid(w.w));
+    return d;
+}
+
+// Multiplicity from the reduced weight sum S, the anchor and a ready Exp(1).
+// (e^{-beta 0} = 1 exactly, so the anchor exponential is skipped at A = 0.)
+__device__ __forceinline__ double multiplicity_e1(uint64_t S, int32_t k, float beta, float anchor, float e1,
+                                                  int *sat) {
+    float ps = __fmul_rn(__ull2float_rn(S), 0x1p-32f);
+    ps = __fdiv_rn(ps, __int2float_rn(k));
+    const float f = anchor > 0.0f ? det_expf(-__fmul_rn(beta, anchor)) : 1.0f;
+    const float p = __fmul_rn(ps, f);
+    *sat = 0;
+    if (p >= 1.0f) return 1.0;
+    if (p <= 0.0f) {
+        *sat = 1;
+        return 9223372036854775808.0;
+    }
+    const float g = __fdiv_rn(e1, det_neg_log1m(p));
+    if (!(g < 0x1p63f)) {
+        *sat = 1;
+        return 9223372036854775808.0;
+    }
+    return __dadd_rn(static_cast<double>(floorf(g)), 1.0);
+}
+
+// First k distinct values of v_m = floor(word_m n / 2^32), m = 0, 1, ...,
+// drawn by one warp into `list`.  Returns false when the draw cap is hit.
+__device__ __forceinline__ bool draw_subset_warp(uint64_t seed, uint32_t chain, uint64_t sstep, int n, int k,
+                                                 int ld, int32_t *list, uint32_t *bitmap, int lane) {
+    for (int w = lane; w < ld / 32; w += 32) bitmap[w] = 0u;
+    __syncwarp();
+    const uint32_t cap = 64u * static_cast<uint32_t>(n) + 1024u;
+    int got = 0;
+    uint32_t m0 = 0;
+    while (got < k) {
+        const uint32_t m = m0 + lane;
+        const bool valid = m < cap;
+        const uint32_t word = rng_word(seed, TAG_SUBSET, chain, sstep, m);
+        const uint32_t v = __umulhi(word, static_cast<uint32_t>(n));
+        const uint32_t eq = __match_any_sync(0xFFFFFFFFu, valid ? v : 0xFFFFFFFFu);
+        const bool first = (__ffs(eq) - 1) == lane;
+        const bool seen = (bitmap[v >> 5] >> (v & 31u)) & 1u;
+        const bool acc = valid && first && !seen;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, acc);
+        const int rank = got + __popc(bal & ((1u << lane) - 1u));
+        if (acc && rank < k) list[rank] = static_cast<int32_t>(v);
+        if (acc) atomicOr(&bitmap[v >> 5], 1u << (v & 31u));
+        got += __popc(bal);
+        m0 += 32;
+        __syncwarp();
+        if (got < k && m0 >= cap) return false;
+    }
+    return true;
+}
+
+constexpr int CPT = 4;  // candidates per consumer thread kept in registers
+constexpr int PF = 4;   // row chunks per consumer thread loaded ahead of the move
+
 // ---------------------------------------------------------------------------
-// The kernel.
+// The kernel.  TC consumer warps per chain; P.prod producer warps (0 or 1).
 // ---------------------------------------------------------------------------
-template <typename QT, typename HT, int T, bool CSR>
-__global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const KParams P) {
+template <typename QT, typename HT, int TC, bool CSR>
+__global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const KParams P) {
     using A = Arith<HT>;
     using D = typename A::D;
     using CT = typename A::C;
-    constexpr int TT = 32 * T;  // threads per team
+    constexpr int TCC = 32 * TC;  // consumer threads per team
 
     extern __shared__ __align__(16) unsigned char smem[];
     const CtaDesc cd = P.cta[blockIdx.x];
+    const int prod = P.prod;
+    const int TT = TCC + 32 * prod;  // team threads
     const int team = threadIdx.x / TT;
     if (team >= cd.count) return;  // idle warps take part in no barrier
     const int tid = threadIdx.x - team * TT;
     const int lane = threadIdx.x & 31;
     const int wit = tid >> 5;
+    const bool consumer = wit < TC;
     const int cid = P.cta_chains[cd.first + team];
     const ChainDesc chd = P.chain[cid];
     const InstDesc in = P.inst[chd.inst];
@@ -144,9 +217,10 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
     const int ld = in.ld;
     const int variant = P.variant;
     const bool use_list = needs_list(variant, P.subset);
+    const bool slot_list = prod > 0 && variant == VAR_BASIC;
     const int k = (variant == VAR_RF) ? n : (variant == VAR_METROPOLIS ? 1 : in.k);
 
-    const ChainSmem L = chain_smem(ld, k, static_cast<int32_t>(sizeof(HT)), use_list);
+    const ChainSmem L = chain_smem(ld, k, static_cast<int32_t>(sizeof(HT)), use_list, prod > 0, slot_list);
     unsigned char *base = smem + chd.smem_off;
     HT *h = reinterpret_cast<HT *>(base + L.fields);
     uint32_t *xw = reinterpret_cast<uint32_t *>(base + L.xw);
@@ -157,9 +231,26 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
     int32_t *pub_b = reinterpret_cast<int32_t *>(base + L.scratch + 648);
     int32_t *swap_cnt = reinterpret_cast<int32_t *>(base + L.scratch + 652);
     int32_t *dead_slot = reinterpret_cast<int32_t *>(base + L.scratch + 656);
+    // "another record follows", one word per record parity: the consumers
+    // write record r's word before the barrier ending r; the producer reads it
+    // after that barrier, and the same word is rewritten only after the
+    // producer has reached the next barrier.
+    int32_t *more_slot = reinterpret_cast<int32_t *>(base + L.scratch + 660);
 
     const CT *bvec = reinterpret_cast<const CT *>(in.b);
     const CT *dvec = reinterpret_cast<const CT *>(in.diag);
+
+    // named barriers: 1 + 2 team (whole team), 2 + 2 team (consumers), then groups
+    const int bar_all = 1 + 2 * team;
+    const int bar_cons = 2 + 2 * team;
+    auto sync_all = [&]() {
+        if (TT == 32) __syncwarp();
+        else named_sync(bar_all, TT);
+    };
+    auto sync_cons = [&]() {
+        if constexpr (TC == 1) __syncwarp();
+        else named_sync(bar_cons, TCC);
+    };
 
     // ---- load the chain ----------------------------------------------------
     {
@@ -173,58 +264,71 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
     if (tid == 0) {
         *swap_cnt = 0;
         *dead_slot = 0;
+        more_slot[0] = 1;
+        more_slot[1] = 1;
     }
     ChainState st = P.state[cid];
-    float beta = in.betas[st.beta_idx];
     const uint64_t seed = P.seed;
     const uint32_t chain_id = static_cast<uint32_t>(cid);
+    sync_all();
+
+    // ---- producer: state-independent draws for record `step` into slot `s` --
+    auto produce = [&](int s, uint64_t step) {
+        unsigned char *slot = base + L.slots + s * L.slot_bytes;
+        float *ex = reinterpret_cast<float *>(slot + 16);
+        const int ptid = tid - TCC;
+        const int pthreads = 32 * prod;
+        const int blocks = (k + 3) >> 2;
+        for (int b = ptid; b < blocks; b += pthreads) {
+            const uint4 w = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(b));
+            const int t = 4 * b;
+            ex[t] = race_exp(w.x);
+            if (t + 1 < k) ex[t + 1] = race_exp(w.y);
+            if (t + 2 < k) ex[t + 2] = race_exp(w.z);
+            if (t + 3 < k) ex[t + 3] = race_exp(w.w);
+        }
+        if (ptid == pthreads - 1) {
+            const RecordDraws d = record_draws(seed, chain_id, step, n);
+            reinterpret_cast<float *>(slot)[0] = d.e1;
+            reinterpret_cast<int32_t *>(slot)[1] = d.mi;
+            reinterpret_cast<float *>(slot)[2] = d.mlu;
+        }
+        if (slot_list && wit == TC) {
+            int32_t *sl = reinterpret_cast<int32_t *>(slot + 16 + 4 * k);
+            const bool ok = draw_subset_warp(seed, chain_id, step, n, k, ld, sl, bitmap, lane);
+            if (lane == 0) reinterpret_cast<int32_t *>(slot)[3] = ok ? 0 : 1;
+        }
+    };
+
+    if (!consumer) {
+        // The producer runs one record ahead of the consumers; it leaves when
+        // they report that no record follows.
+        uint64_t step = static_cast<uint64_t>(st.step);
+        int s = 0;
+        produce(0, step);
+        sync_all();
+        while (true) {
+            produce(s ^ 1, step + 1);
+            sync_all();  // end of the consumers' record that used slot s
+            if (!more_slot[s]) break;
+            s ^= 1;
+            step += 1;
+        }
+        return;
+    }
+
+    // ---- consumers ------------------------------------------------------------
+    const int ctid = tid;
+    float beta = in.betas[st.beta_idx];
     int dead = 0;
     bool list_valid = false;
     int64_t tape_pos = 0;
-    team_sync<T>(team);
+    int cur = 0;  // current slot
+    if (prod > 0) sync_all();  // slot 0 ready
 
-    // Draw the random subset for stream step `sstep` into `list` (warp 0 of
-    // the team).  The set is the first k distinct values of
-    // v_m = floor(word_m n / 2^32), m = 0, 1, ...
-    auto draw_subset = [&](uint64_t sstep) {
-        if (wit == 0) {
-            for (int w = lane; w < ld / 32; w += 32) bitmap[w] = 0u;
-            __syncwarp();
-            const uint32_t cap = 64u * static_cast<uint32_t>(n) + 1024u;
-            int got = 0;
-            uint32_t m0 = 0;
-            while (got < k) {
-                const uint32_t m = m0 + lane;
-                const bool valid = m < cap;
-                const uint32_t word = rng_word(seed, TAG_SUBSET, chain_id, sstep, m);
-                const uint32_t v = __umulhi(word, static_cast<uint32_t>(n));
-                const uint32_t eq = __match_any_sync(0xFFFFFFFFu, valid ? v : 0xFFFFFFFFu);
-                const bool first = (__ffs(eq) - 1) == lane;
-                const bool seen = (bitmap[v >> 5] >> (v & 31u)) & 1u;
-                const bool acc = valid && first && !seen;
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, acc);
-                const int rank = got + __popc(bal & ((1u << lane) - 1u));
-                if (acc && rank < k) list[rank] = static_cast<int32_t>(v);
-                if (acc) atomicOr(&bitmap[v >> 5], 1u << (v & 31u));
-                got += __popc(bal);
-                m0 += 32;
-                __syncwarp();
-                if (got < k && m0 >= cap) {
-                    if (lane == 0) set_status(P.status, ST_TIMEOUT);
-                    dead = 1;
-                    break;
-                }
-            }
-            if (lane == 0) *dead_slot = dead;
-        }
-        team_sync<T>(team);
-        if constexpr (T > 1) dead = *dead_slot;
-    };
-
-    // Candidate bit of position t.
-    auto cand = [&](int t) -> int {
+    auto cand = [&](int t, const int32_t *sl) -> int {
         if (variant == VAR_RF) return t;
-        if (use_list) return list[t];
+        if (use_list) return sl[t];
         int c = st.set_start + t;
         return c >= n ? c - n : c;
     };
@@ -234,13 +338,28 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
         return A::delta(h[i], bvec[i], dvec[i], xi);
     };
 
-    // Apply the move to bit j (all team threads), then flip x_j.
-    auto apply_move = [&](int j) {
+    // Dense row j: chunks [0, PF * TCC) are loaded into registers first.
+    constexpr int VE = 16 / static_cast<int>(sizeof(QT));
+    uint4 pre[PF];
+    auto prefetch_row = [&](int j) {
+        if constexpr (!CSR) {
+            const QT *row = reinterpret_cast<const QT *>(in.q) + static_cast<int64_t>(j) * ld;
+            const int chunks = ld / VE;
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int c = ctid + u * TCC;
+                if (c < chunks) pre[u] = ld_nc_v4(row + c * VE);
+            }
+        }
+    };
+
+    // Apply the move to bit j (all consumer threads), then flip x_j.
+    auto apply_move = [&](int j, bool prefetched) {
         const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
         if constexpr (CSR) {
             const int e0 = in.row_ptr[j], e1 = in.row_ptr[j + 1];
             const QT *vals = reinterpret_cast<const QT *>(in.q);
-            for (int e = e0 + tid; e < e1; e += TT) {
+            for (int e = e0 + ctid; e < e1; e += TCC) {
                 const int r = in.col[e];
                 const QT qv = vals[e];
                 if constexpr (std::is_same<HT, float>::value) {
@@ -250,7 +369,7 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
                                               : static_cast<int32_t>(h[r]) - static_cast<int32_t>(qv));
                 }
             }
-            if (tid == TT - 1) {
+            if (ctid == TCC - 1) {
                 const CT dv = dvec[j];
                 if constexpr (std::is_same<HT, float>::value) {
                     h[j] = up ? __fadd_rn(h[j], dv) : __fsub_rn(h[j], dv);
@@ -259,32 +378,33 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
                 }
             }
         } else {
-            constexpr int VE = 16 / static_cast<int>(sizeof(QT));
             const QT *row = reinterpret_cast<const QT *>(in.q) + static_cast<int64_t>(j) * ld;
             const int chunks = ld / VE;
-            int c = tid;
-            // four independent 16-byte loads in flight per thread
-            for (; c + 3 * TT < chunks; c += 4 * TT) {
-                const uint4 v0 = ld_nc_v4(row + (c + 0 * TT) * VE);
-                const uint4 v1 = ld_nc_v4(row + (c + 1 * TT) * VE);
-                const uint4 v2 = ld_nc_v4(row + (c + 2 * TT) * VE);
-                const uint4 v3 = ld_nc_v4(row + (c + 3 * TT) * VE);
-                add_chunk<QT, HT>(h + (c + 0 * TT) * VE, v0, up);
-                add_chunk<QT, HT>(h + (c + 1 * TT) * VE, v1, up);
-                add_chunk<QT, HT>(h + (c + 2 * TT) * VE, v2, up);
-                add_chunk<QT, HT>(h + (c + 3 * TT) * VE, v3, up);
+            if (!prefetched) prefetch_row(j);
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int c = ctid + u * TCC;
+                if (c < chunks) add_chunk<QT, HT>(h + c * VE, pre[u], up);
             }
-            for (; c < chunks; c += TT) {
-                const uint4 v0 = ld_nc_v4(row + c * VE);
-                add_chunk<QT, HT>(h + c * VE, v0, up);
+            int c = ctid + PF * TCC;
+            for (; c + 3 * TCC < chunks; c += 4 * TCC) {
+                const uint4 v0 = ld_nc_v4(row + (c + 0 * TCC) * VE);
+                const uint4 v1 = ld_nc_v4(row + (c + 1 * TCC) * VE);
+                const uint4 v2 = ld_nc_v4(row + (c + 2 * TCC) * VE);
+                const uint4 v3 = ld_nc_v4(row + (c + 3 * TCC) * VE);
+                add_chunk<QT, HT>(h + (c + 0 * TCC) * VE, v0, up);
+                add_chunk<QT, HT>(h + (c + 1 * TCC) * VE, v1, up);
+                add_chunk<QT, HT>(h + (c + 2 * TCC) * VE, v2, up);
+                add_chunk<QT, HT>(h + (c + 3 * TCC) * VE, v3, up);
             }
+            for (; c < chunks; c += TCC) add_chunk<QT, HT>(h + c * VE, ld_nc_v4(row + c * VE), up);
         }
-        team_sync<T>(team);  // every thread has read x_j
-        if (tid == 0) xw[j >> 5] ^= 1u << (j & 31);
+        sync_cons();  // every consumer has read x_j
+        if (ctid == 0) xw[j >> 5] ^= 1u << (j & 31);
     };
 
     auto write_record = [&](int32_t flip, double m) {
-        if (tid == 0 && P.tape && tape_pos < P.tape_cap) {
+        if (ctid == 0 && P.tape && tape_pos < P.tape_cap) {
             const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos;
             P.tape_flip[o] = flip;
             P.tape_m[o] = m;
@@ -292,19 +412,32 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
         tape_pos += 1;
     };
 
+    // Race exponential of position t in the current record.
+    auto ex_of = [&](int t, uint64_t step) -> float {
+        if (prod > 0) return reinterpret_cast<const float *>(base + L.slots + cur * L.slot_bytes + 16)[t];
+        return race_exp(rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t)));
+    };
+
     // One record.  Returns true when the record was an Unbiased period end.
     auto one_record = [&]() -> bool {
         const uint64_t step = static_cast<uint64_t>(st.step);
+        const unsigned char *slot = base + L.slots + cur * L.slot_bytes;
+        RecordDraws rd;
+        if (prod > 0) {
+            rd.e1 = reinterpret_cast<const float *>(slot)[0];
+            rd.mi = reinterpret_cast<const int32_t *>(slot)[1];
+            rd.mlu = reinterpret_cast<const float *>(slot)[2];
+        } else {
+            rd = record_draws(seed, chain_id, step, n);
+        }
         bool period_end = false;
         if (variant == VAR_METROPOLIS) {
-            const uint4 wv = rng_block(seed, TAG_STEP, chain_id, step, 0);
-            const int i = static_cast<int>(__umulhi(wv.z, static_cast<uint32_t>(n)));
+            const int i = rd.mi;
             const D d = delta_of(i);
-            const float lu = det_logf(u01_grid(wv.w));
             const float y = -__fmul_rn(beta, A::tof(d));
-            team_sync<T>(team);  // all reads of h / x done before the move
-            if (lu < y) {
-                apply_move(i);
+            sync_cons();  // all reads of h / x done before the move
+            if (rd.mlu < y) {
+                apply_move(i, false);
                 st.E = __dadd_rn(st.E, A::tod(d));
                 st.flips += 1;
                 write_record(i, 1.0);
@@ -314,61 +447,106 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
             }
             st.sum_m = __dadd_rn(st.sum_m, 1.0);
         } else {
+            const int32_t *sl = list;
             if (variant == VAR_BASIC) {
-                draw_subset(step);
+                if (prod > 0) {
+                    sl = reinterpret_cast<const int32_t *>(slot + 16 + 4 * k);
+                    if (reinterpret_cast<const int32_t *>(slot)[3]) {
+                        if (ctid == 0) set_status(P.status, ST_TIMEOUT);
+                        dead = 1;
+                    }
+                } else {
+                    if (wit == 0 && !draw_subset_warp(seed, chain_id, step, n, k, ld, list, bitmap, lane)) {
+                        if (lane == 0) {
+                            set_status(P.status, ST_TIMEOUT);
+                            *dead_slot = 1;
+                        }
+                    }
+                    sync_cons();
+                    dead = *dead_slot;
+                }
             } else if (use_list && !list_valid) {
-                draw_subset(static_cast<uint64_t>(st.period_start));
+                if (wit == 0 &&
+                    !draw_subset_warp(seed, chain_id, static_cast<uint64_t>(st.period_start), n, k, ld, list, bitmap,
+                                      lane)) {
+                    if (lane == 0) {
+                        set_status(P.status, ST_TIMEOUT);
+                        *dead_slot = 1;
+                    }
+                }
+                sync_cons();
+                dead = *dead_slot;
                 list_valid = true;
             }
             if (dead) return true;
-            // a2 + a3: anchor
+            const bool fast = k <= CPT * TCC;
+            // a2 + a3: deltas and the anchor
+            D dl[CPT];
             uint32_t lmin = 0xFFFFFFFFu;
-            for (int t = tid; t < k; t += TT) {
-                const uint32_t kd = A::key(A::pos(delta_of(cand(t))));
-                lmin = kd < lmin ? kd : lmin;
+            if (fast) {
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) {
+                    const int t = ctid + u * TCC;
+                    if (t < k) {
+                        dl[u] = delta_of(cand(t, sl));
+                        const uint32_t kd = A::key(A::pos(dl[u]));
+                        lmin = kd < lmin ? kd : lmin;
+                    }
+                }
+            } else {
+                for (int t = ctid; t < k; t += TCC) {
+                    const uint32_t kd = A::key(A::pos(delta_of(cand(t, sl))));
+                    lmin = kd < lmin ? kd : lmin;
+                }
             }
             uint32_t amin_k = __reduce_min_sync(0xFFFFFFFFu, lmin);
-            if constexpr (T > 1) {
+            if constexpr (TC > 1) {
                 if (lane == 0) red[0 * 32 + wit] = amin_k;
-                team_sync<T>(team);
+                sync_cons();
                 amin_k = red[0];
 #pragma unroll 4
-                for (int w = 1; w < T; ++w) amin_k = red[w] < amin_k ? red[w] : amin_k;
+                for (int w = 1; w < TC; ++w) amin_k = red[w] < amin_k ? red[w] : amin_k;
             }
             const D amin = A::unkey(amin_k);
             // a4: weights, race, quantised sum
             uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
-            for (int t = tid; t < k; t += TT) {
-                const D dp = A::pos(delta_of(cand(t)));
-                const float w = det_expf(-__fmul_rn(beta, A::diff(dp, amin)));
+            auto visit = [&](int t, D dv) {
+                const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dv), amin)));
                 const uint64_t qw = __float2ull_rz(__fmul_rn(w, 0x1p32f));
                 sa += static_cast<uint32_t>(qw >> 16);
                 sb += static_cast<uint32_t>(qw & 0xFFFFull);
-                const uint32_t word = rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t));
-                const float ex = det_neg_log1m(u01_fine(word));
-                const uint32_t kb = __float_as_uint(__fdiv_rn(ex, w));
-                if (kb < bkey) {  // t ascending: the first minimum is kept
+                const uint32_t kb = __float_as_uint(__fdiv_rn(ex_of(t, step), w));
+                if (kb < bkey) {  // t ascending per thread: the first minimum is kept
                     bkey = kb;
                     bpos = static_cast<uint32_t>(t);
                 }
+            };
+            if (fast) {
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) {
+                    const int t = ctid + u * TCC;
+                    if (t < k) visit(t, dl[u]);
+                }
+            } else {
+                for (int t = ctid; t < k; t += TCC) visit(t, delta_of(cand(t, sl)));
             }
             uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
             uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
-            uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa);
-            uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
+            const uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa);
+            const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
             uint64_t S;
-            if constexpr (T > 1) {
+            if constexpr (TC > 1) {
                 if (lane == 0) {
                     red[1 * 32 + wit] = wkey;
                     red[2 * 32 + wit] = wpos;
                     red[3 * 32 + wit] = SA;
                     red[4 * 32 + wit] = SB;
                 }
-                team_sync<T>(team);
+                sync_cons();
                 wkey = red[32];
                 wpos = red[64];
                 uint64_t SA64 = red[96], SB64 = red[128];
-                for (int w = 1; w < T; ++w) {
+                for (int w = 1; w < TC; ++w) {
                     const uint32_t kk = red[32 + w], pp = red[64 + w];
                     if (kk < wkey || (kk == wkey && pp < wpos)) {
                         wkey = kk;
@@ -381,14 +559,15 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
             } else {
                 S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
             }
+            const int j = cand(static_cast<int>(wpos), sl);
+            // Basic and RF always move: start the row load before the multiplicity
+            const bool always_move = variant != VAR_UNBIASED;
+            if (always_move) prefetch_row(j);
             // a5: multiplicity and budget
-            const uint4 wv = rng_block(seed, TAG_STEP, chain_id, step, 0);
-            float p;
             int sat;
-            double m = multiplicity(S, k, beta, A::tof(amin), wv.x, wv.y, &p, &sat);
-            const int j = cand(static_cast<int>(wpos));
+            double m = multiplicity_e1(S, k, beta, A::tof(amin), rd.e1, &sat);
             const D dj = delta_of(j);
-            team_sync<T>(team);  // reads of h, x, list done
+            sync_cons();  // reads of h, x and the list are done
             bool move = true;
             if (variant == VAR_UNBIASED) {
                 if (m <= static_cast<double>(st.L)) {
@@ -408,7 +587,7 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
             }
             if (move) {
                 if (sat) st.saturated += 1;
-                apply_move(j);
+                apply_move(j, always_move);
                 st.E = __dadd_rn(st.E, A::tod(dj));
                 st.flips += 1;
                 write_record(j, m);
@@ -419,92 +598,105 @@ __global__ void __launch_bounds__(T == 32 ? 1024 : 512) pns_sample_kernel(const 
         }
         if (st.E < st.best_E) st.best_E = st.E;
         st.step += 1;
-        team_sync<T>(team);
+        sync_cons();
         return period_end;
+    };
+
+    // Ends a record: tell the producer whether another one follows.
+    auto end_record = [&](bool more) {
+        if (prod > 0) {
+            if (ctid == 0) more_slot[cur] = more ? 1 : 0;
+            sync_all();
+            cur ^= 1;
+        }
     };
 
     // ---- main loop -----------------------------------------------------------
     if (!P.pt) {
-        for (int64_t r = 0; r < P.steps && !dead; ++r) one_record();
+        if (P.steps <= 0) end_record(false);
+        for (int64_t r = 0; r < P.steps; ++r) {
+            one_record();
+            const bool more = r + 1 < P.steps && !dead;
+            end_record(more);
+            if (!more) break;
+        }
     } else {
         const int R = P.R;
-        const int gbar = (T == 1 ? 1 : 1 + cd.count) + team / R;  // named barrier of the group
-        const int gthreads = R * TT;
+        // named barrier of the exchange group, after the ids the teams use
+        const int gbar = (TT > 32 ? 1 + 2 * cd.count : 1) + team / R;
+        const int gthreads = R * TCC;
         const int64_t rounds = P.steps / P.swap_interval;
         const int64_t per_round = variant == VAR_UNBIASED ? P.swap_interval / P.L0 : P.swap_interval;
-        for (int64_t rd = 0; rd < rounds; ++rd) {
-            if (variant == VAR_UNBIASED) {
-                int64_t periods = 0;
-                while (periods < per_round) {
-                    if (dead) { periods = per_round; break; }
-                    if (one_record()) periods += 1;
-                }
-            } else {
-                for (int64_t r = 0; r < per_round && !dead; ++r) one_record();
-            }
-            if (tid == 0) {
-                *pub_E = st.E;
-                *pub_b = st.beta_idx;
-            }
-            named_sync(gbar, gthreads);
-            if (chd.slot == 0 && tid == 0) {
-                // exchange round for this group; slots of the group are the R
-                // consecutive teams starting at this one
-                const uint64_t done = static_cast<uint64_t>(st.sum_m) / static_cast<uint64_t>(P.swap_interval);
-                const uint64_t rnd = done - 1;
-                const ChainDesc *cds = P.chain;
-                int slot_of[32];
-                for (int s = 0; s < R; ++s) {
-                    const int oc = P.cta_chains[cd.first + team + s];
-                    const unsigned char *ob = smem + cds[oc].smem_off;
-                    slot_of[*reinterpret_cast<const int32_t *>(ob + L.scratch + 648)] = s;
-                }
-                int q = 0;
-                for (int a = static_cast<int>(rnd & 1u); a + 1 < R; a += 2, ++q) {
-                    const int sa_ = slot_of[a], sb_ = slot_of[a + 1];
-                    const int ca = P.cta_chains[cd.first + team + sa_];
-                    const int cb = P.cta_chains[cd.first + team + sb_];
-                    unsigned char *pa = smem + cds[ca].smem_off + L.scratch;
-                    unsigned char *pb = smem + cds[cb].smem_off + L.scratch;
-                    const double Ea = *reinterpret_cast<double *>(pa + 640);
-                    const double Eb = *reinterpret_cast<double *>(pb + 640);
-                    const float db = __fsub_rn(in.betas[a], in.betas[a + 1]);
-                    const float de = __double2float_rn(__dsub_rn(Ea, Eb));
-                    const float xr = __fmul_rn(db, de);
-                    const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd.group), rnd,
-                                                static_cast<uint32_t>(q));
-                    if (det_logf(u01_grid(w)) < xr) {
-                        *reinterpret_cast<int32_t *>(pa + 648) = a + 1;
-                        *reinterpret_cast<int32_t *>(pb + 648) = a;
-                        slot_of[a] = sb_;
-                        slot_of[a + 1] = sa_;
-                        // count on both chains' published slot: use the high bit area
-                        atomicAdd(reinterpret_cast<int32_t *>(pa + 652), 1);
-                        atomicAdd(reinterpret_cast<int32_t *>(pb + 652), 1);
+        if (rounds <= 0) end_record(false);
+        for (int64_t rdi = 0; rdi < rounds; ++rdi) {
+            int64_t done = 0;
+            while (done < per_round) {
+                const bool pend = dead ? true : one_record();
+                if (variant != VAR_UNBIASED || pend) done += 1;
+                if (done == per_round) {
+                    // exchange round among the R replicas of this group
+                    if (ctid == 0) {
+                        *pub_E = st.E;
+                        *pub_b = st.beta_idx;
                     }
+                    named_sync(gbar, gthreads);
+                    if (chd.slot == 0 && ctid == 0) {
+                        const uint64_t ndone =
+                            static_cast<uint64_t>(st.sum_m) / static_cast<uint64_t>(P.swap_interval);
+                        const uint64_t rnd = ndone - 1;
+                        int slot_of[32];
+                        for (int s2 = 0; s2 < R; ++s2) {
+                            const int oc = P.cta_chains[cd.first + team + s2];
+                            const unsigned char *ob = smem + P.chain[oc].smem_off;
+                            slot_of[*reinterpret_cast<const int32_t *>(ob + L.scratch + 648)] = s2;
+                        }
+                        int q = 0;
+                        for (int a = static_cast<int>(rnd & 1u); a + 1 < R; a += 2, ++q) {
+                            const int sa_ = slot_of[a], sb_ = slot_of[a + 1];
+                            const int ca = P.cta_chains[cd.first + team + sa_];
+                            const int cb = P.cta_chains[cd.first + team + sb_];
+                            unsigned char *pa = smem + P.chain[ca].smem_off + L.scratch;
+                            unsigned char *pb = smem + P.chain[cb].smem_off + L.scratch;
+                            const double Ea = *reinterpret_cast<double *>(pa + 640);
+                            const double Eb = *reinterpret_cast<double *>(pb + 640);
+                            const float db = __fsub_rn(in.betas[a], in.betas[a + 1]);
+                            const float de = __double2float_rn(__dsub_rn(Ea, Eb));
+                            const float xr = __fmul_rn(db, de);
+                            const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd.group), rnd,
+                                                        static_cast<uint32_t>(q));
+                            if (det_logf(u01_grid(w)) < xr) {
+                                *reinterpret_cast<int32_t *>(pa + 648) = a + 1;
+                                *reinterpret_cast<int32_t *>(pb + 648) = a;
+                                slot_of[a] = sb_;
+                                slot_of[a + 1] = sa_;
+                                atomicAdd(reinterpret_cast<int32_t *>(pa + 652), 1);
+                                atomicAdd(reinterpret_cast<int32_t *>(pb + 652), 1);
+                            }
+                        }
+                    }
+                    named_sync(gbar, gthreads);
+                    st.beta_idx = *pub_b;
+                    st.swaps += *swap_cnt;
+                    sync_cons();
+                    if (ctid == 0) *swap_cnt = 0;
+                    beta = in.betas[st.beta_idx];
                 }
+                end_record(!(done == per_round && rdi + 1 == rounds));
             }
-            named_sync(gbar, gthreads);
-            st.beta_idx = *pub_b;
-            st.swaps += *swap_cnt;
-            team_sync<T>(team);
-            if (tid == 0) *swap_cnt = 0;
-            beta = in.betas[st.beta_idx];
-            team_sync<T>(team);
         }
     }
 
-    // ---- write the chain back ------------------------------------------------
-    team_sync<T>(team);
+    // ---- write the chain back (consumers) --------------------------------------
+    sync_cons();
     {
         HT *gh = reinterpret_cast<HT *>(P.fields) + static_cast<int64_t>(cid) * P.LD;
         uint32_t *gx = P.xbits + static_cast<int64_t>(cid) * P.W;
         const int hchunks = ld * static_cast<int>(sizeof(HT)) / 16;
-        for (int c = tid; c < hchunks; c += TT)
+        for (int c = ctid; c < hchunks; c += TCC)
             reinterpret_cast<uint4 *>(gh)[c] = reinterpret_cast<const uint4 *>(h)[c];
-        for (int w = tid; w < ld / 32; w += TT) gx[w] = xw[w];
+        for (int w = ctid; w < ld / 32; w += TCC) gx[w] = xw[w];
     }
-    if (tid == 0) {
+    if (ctid == 0) {
         st.tape_records = tape_pos < P.tape_cap ? tape_pos : P.tape_cap;
         if (!P.tape) st.tape_records = 0;
         P.state[cid] = st;

@@ -40,7 +40,8 @@ class pns_problem(C.Structure):
 class pns_config(C.Structure):
     _fields_ = [("variant", C.c_int32), ("k", C.c_int32), ("subset", C.c_int32), ("chains_per_replica", C.c_int32),
                 ("L0", C.c_int64), ("swap_interval", C.c_int64), ("seed", C.c_uint64), ("tape", C.c_int32),
-                ("warps_per_chain", C.c_int32), ("x0", C.c_void_p)]
+                ("warps_per_chain", C.c_int32), ("chains_per_cta", C.c_int32), ("reserved", C.c_int32),
+                ("x0", C.c_void_p)]
 
 
 class pns_info(C.Structure):
@@ -62,7 +63,7 @@ STATS_DTYPE = np.dtype([("steps", np.int64), ("flips", np.int64), ("stays", np.i
                         ("sum_m", np.float64), ("best_energy", np.float64)])
 assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
 
-EXPORTS = ("pns_create", "pns_run", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore",
+EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore",
            "pns_destroy", "pns_last_error")
 
 _lib = None
@@ -79,6 +80,7 @@ def lib():
         vp = C.c_void_p
         L.pns_create.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(vp)]
         L.pns_run.argtypes = [vp, C.c_int64, vp]
+        L.pns_run_plain.argtypes = [vp, C.c_int64, vp]
         L.pns_read.argtypes = [vp, vp, vp, vp, vp, vp]
         L.pns_fields.argtypes = [vp, vp, vp]
         L.pns_get_info.argtypes = [vp, vp]
@@ -88,7 +90,7 @@ def lib():
         L.pns_destroy.restype = None
         L.pns_last_error.argtypes = []
         L.pns_last_error.restype = C.c_char_p
-        for name in ("pns_create", "pns_run", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint",
+        for name in ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint",
                      "pns_restore"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -177,7 +179,7 @@ def make_problem(n, q=None, b=None, betas=(1.0,), csr=None, k=0, keep=None):
 
 
 def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100, swap_interval=0, seed=0,
-                tape=False, warps_per_chain=0, x0=None):
+                tape=False, warps_per_chain=0, x0=None, chains_per_cta=0):
     c = pns_config()
     c.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     c.k = int(k)
@@ -188,6 +190,7 @@ def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica
     c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     c.tape = int(bool(tape))
     c.warps_per_chain = int(warps_per_chain)
+    c.chains_per_cta = int(chains_per_cta)
     c.x0 = _addr(x0)
     return c
 
@@ -201,6 +204,10 @@ def pns_create(problems, config, stream=None):
 
 def pns_run(ctx, steps, stream=None):
     _check(lib().pns_run(ctx, int(steps), _stream(stream)))
+
+
+def pns_run_plain(ctx, steps, stream=None):
+    _check(lib().pns_run_plain(ctx, int(steps), _stream(stream)))
 
 
 def pns_get_info(ctx):
@@ -240,20 +247,24 @@ class Sampler:
     and returns numpy results."""
 
     def __init__(self, problems, variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100,
-                 swap_interval=0, seed=0, tape=False, warps_per_chain=0, x0=None, stream=None):
+                 swap_interval=0, seed=0, tape=False, warps_per_chain=0, x0=None, stream=None, chains_per_cta=0):
         keep = []
         probs = []
         for pr in problems:
             probs.append(make_problem(keep=keep, **pr))
         if x0 is not None:
             keep.append(x0)
-        cfg = make_config(variant, k, subset, chains_per_replica, L0, swap_interval, seed, tape, warps_per_chain, x0)
+        cfg = make_config(variant, k, subset, chains_per_replica, L0, swap_interval, seed, tape, warps_per_chain, x0,
+                          chains_per_cta)
         self.ctx = pns_create(probs, cfg, stream)
         self.info = pns_get_info(self.ctx)
         self.tape = bool(tape)
 
     def run(self, steps, stream=None):
         pns_run(self.ctx, steps, stream)
+
+    def run_plain(self, steps, stream=None):
+        pns_run_plain(self.ctx, steps, stream)
 
     def read(self, stream=None, tape=True):
         info = pns_get_info(self.ctx)

@@ -341,6 +341,81 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def side_workload(args):
+    """Other benchmark shapes, one JSON line each (not the headline):
+    tempering -- 512 fp32 instances, n uniform in [128, 2048], 8 replicas on a
+                 geometric beta ladder 0.1..10, Unbiased PNS k = n // 16,
+                 exchange every L0 = 100 original samples; one step = 1000
+                 original samples (10 exchange rounds) for every chain.
+    lattice   -- 256 x 256 periodic +-1 lattice (n = 65536) as CSR, 64 chains
+                 for each beta in {0.2, 0.44, 1.0}, Unbiased k = 1024; one step
+                 = `--records` records for every chain."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    if args.workload == "tempering":
+        n_inst = args.instances
+        probs, ladder = synth.workload_tempering(n_inst, seed=args.seed)
+        plist = []
+        for pr in probs:
+            plist.append(dict(n=pr["n"], q=torch.from_numpy(pr["q"]).to(dev), betas=ladder, k=max(1, pr["n"] // 16)))
+        s = pns.Sampler(plist, variant="unbiased", k=1, chains_per_replica=1, L0=100, swap_interval=100,
+                        seed=args.seed, tape=False)
+        per_step = 1000
+        ns = np.repeat(np.array([pr["n"] for pr in probs]), len(ladder))
+        row_bytes = 4 * ns
+        desc = ("tempering: %d fp32 instances n~U[128,2048], 8 replicas (beta 0.1..10), Unbiased k=n/16, "
+                "swap every 100 original samples, 1000 original samples per chain per step" % n_inst)
+    else:
+        side = 256
+        csr = synth.lattice_csr(side, seed=args.seed)
+        csr_d = tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in csr)
+        s = pns.Sampler([dict(n=side * side, csr=csr_d, betas=[0.2, 0.44, 1.0])], variant="unbiased", k=1024,
+                        chains_per_replica=64, L0=100, seed=args.seed, tape=False)
+        per_step = args.records
+        row_bytes = np.full(s.info.chains, 5 * 4 + 4, dtype=np.int64)
+        desc = ("lattice: 256x256 periodic +-1 couplings, CSR, 64 chains x beta {0.2,0.44,1.0}, Unbiased k=1024, "
+                "%d records per chain per step" % per_step)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        s.run(per_step)
+    torch.cuda.synchronize()
+    before = s.read(tape=False)["stats"]
+    ms = []
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_%s.csv" % args.workload), 0)
+    with clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run(per_step)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    after = s.read(tape=False)["stats"]
+    secs = sum(ms) / 1e3
+    flips = (after["flips"] - before["flips"]).astype(np.float64)
+    recs = float((after["steps"] - before["steps"]).sum())
+    byts = float((flips * row_bytes).sum())
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    line = {"metric": "PNS jump samples/s (records/s)", "workload": args.workload, "value": recs / secs,
+            "unit": "samples/s", "flips_per_s": float(flips.sum()) / secs,
+            "original_samples_per_s": float((after["sum_m"] - before["sum_m"]).sum()) / secs,
+            "ms_per_step": secs * 1e3 / args.steps, "steps": args.steps, "warmup": args.warmup,
+            "row_bytes_per_s_GBs": byts / secs / 1e9, "hbm_peak_GBs": hbm, "frac_of_hbm": byts / secs / 1e9 / hbm,
+            "chains": int(s.info.chains), "ctas": int(s.info.ctas), "warps_per_chain": int(s.info.warps_per_chain),
+            "swaps_accepted": int((after["swaps_accepted"] - before["swaps_accepted"]).sum()),
+            "config": {"workload": desc}, "clocks": clk.summary()}
+    s.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,7 +426,14 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the Basic / plain side measurements")
+    ap.add_argument("--workload", default="dense1024", choices=["dense1024", "tempering", "lattice"])
+    ap.add_argument("--instances", type=int, default=512)
     args = ap.parse_args()
+    if args.workload != "dense1024":
+        from paper_2210_10513_gb300 import build as B
+        B.build()
+        side_workload(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -137,24 +137,50 @@ __device__ __forceinline__ RecordDraws record_draws(uint64_t seed, uint32_t chai
 
 // Multiplicity from the reduced weight sum S, the anchor and a ready Exp(1).
 // (e^{-beta 0} = 1 exactly, so the anchor exponential is skipped at A = 0.)
-__device__ __forceinline__ double multiplicity_e1(uint64_t S, int32_t k, float beta, float anchor, float e1,
-                                                  int *sat) {
+// M = floor(g) + 1 is returned twice: as an integer (exact while g < 2^24,
+// which covers every budget test of Unbiased PNS with L0 < 2^24) for the
+// critical path, and as the fp64 record value.  GB300's fp64 pipe has a
+// 64-cycle latency, so nothing on the per-record chain waits for the double.
+struct Mult {
+    int64_t mi;    // M when small (-1: large, use md)
+    double md;     // M as recorded
+    int sat;
+};
+
+__device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float beta, float anchor, float e1) {
+    Mult r;
     float ps = __fmul_rn(__ull2float_rn(S), 0x1p-32f);
     ps = __fdiv_rn(ps, __int2float_rn(k));
     const float f = anchor > 0.0f ? det_expf(-__fmul_rn(beta, anchor)) : 1.0f;
     const float p = __fmul_rn(ps, f);
-    *sat = 0;
-    if (p >= 1.0f) return 1.0;
+    r.sat = 0;
+    if (p >= 1.0f) {
+        r.mi = 1;
+        r.md = 1.0;
+        return r;
+    }
     if (p <= 0.0f) {
-        *sat = 1;
-        return 9223372036854775808.0;
+        r.sat = 1;
+        r.mi = -1;
+        r.md = 9223372036854775808.0;
+        return r;
     }
     const float g = __fdiv_rn(e1, det_neg_log1m(p));
     if (!(g < 0x1p63f)) {
-        *sat = 1;
-        return 9223372036854775808.0;
+        r.sat = 1;
+        r.mi = -1;
+        r.md = 9223372036854775808.0;
+        return r;
     }
-    return __dadd_rn(static_cast<double>(floorf(g)), 1.0);
+    const float fg = floorf(g);
+    if (fg < 16777216.0f) {
+        r.mi = static_cast<int64_t>(__float2int_rz(fg)) + 1;
+        r.md = static_cast<double>(static_cast<int32_t>(r.mi));
+    } else {
+        r.mi = -1;
+        r.md = __dadd_rn(static_cast<double>(fg), 1.0);
+    }
+    return r;
 }
 
 // First k distinct values of v_m = floor(word_m n / 2^32), m = 0, 1, ...,
@@ -403,13 +429,28 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
         if (ctid == 0) xw[j >> 5] ^= 1u << (j & 31);
     };
 
-    auto write_record = [&](int32_t flip, double m) {
-        if (ctid == 0 && P.tape && tape_pos < P.tape_cap) {
-            const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos;
-            P.tape_flip[o] = flip;
-            P.tape_m[o] = m;
+    // Tape and fp64 accumulators are written one record late, so that the
+    // store and the 64-cycle fp64 adds never stall the record that made them.
+    int32_t pend_flip = 0;
+    double pend_m = 0.0;
+    bool pend = false;
+    auto flush_record = [&]() {
+        if (pend) {
+            if (ctid == 0 && P.tape && tape_pos < P.tape_cap) {
+                const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos;
+                P.tape_flip[o] = pend_flip;
+                P.tape_m[o] = pend_m;
+            }
+            tape_pos += 1;
+            pend = false;
         }
-        tape_pos += 1;
+    };
+    auto write_record = [&](int32_t flip, double m) {
+        flush_record();
+        pend_flip = flip;
+        pend_m = m;
+        pend = true;
+        st.sum_m = __dadd_rn(st.sum_m, m);
     };
 
     // Race exponential of position t in the current record.
@@ -445,7 +486,6 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                 st.stays += 1;
                 write_record(-1, 1.0);
             }
-            st.sum_m = __dadd_rn(st.sum_m, 1.0);
         } else {
             const int32_t *sl = list;
             if (variant == VAR_BASIC) {
@@ -564,14 +604,16 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             const bool always_move = variant != VAR_UNBIASED;
             if (always_move) prefetch_row(j);
             // a5: multiplicity and budget
-            int sat;
-            double m = multiplicity_e1(S, k, beta, A::tof(amin), rd.e1, &sat);
+            const Mult mu = multiplicity_e1(S, k, beta, A::tof(amin), rd.e1);
+            double m = mu.md;
+            const int sat = mu.sat;
             const D dj = delta_of(j);
             sync_cons();  // reads of h, x and the list are done
             bool move = true;
             if (variant == VAR_UNBIASED) {
-                if (m <= static_cast<double>(st.L)) {
-                    st.L -= static_cast<int64_t>(m);
+                const bool fits = mu.mi >= 0 ? mu.mi <= st.L : m <= static_cast<double>(st.L);
+                if (fits) {
+                    st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(m);
                 } else {
                     move = false;
                     m = static_cast<double>(st.L);
@@ -594,9 +636,8 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             } else {
                 write_record(-1, m);
             }
-            st.sum_m = __dadd_rn(st.sum_m, m);
         }
-        if (st.E < st.best_E) st.best_E = st.E;
+        st.best_E = fmin(st.best_E, st.E);
         st.step += 1;
         sync_cons();
         return period_end;
@@ -687,6 +728,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
     }
 
     // ---- write the chain back (consumers) --------------------------------------
+    flush_record();
     sync_cons();
     {
         HT *gh = reinterpret_cast<HT *>(P.fields) + static_cast<int64_t>(cid) * P.LD;

@@ -180,6 +180,36 @@ pns_status pns_restore(pns_ctx *ctx, const void *buf, size_t bytes);
 void pns_destroy(pns_ctx *ctx);
 const char *pns_last_error(void);
 
+/* Size of the fixed device array that pns_sample_static works in.  Every GPU
+ * that loads this library holds it until the process exits. */
+#define PNS_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* pns_sample_static -- the paper has no counterpart; this is a convenience for
+ * callers that cannot call cudaMalloc: code running while a framework's
+ * caching allocator owns the device memory, services that allocate only at
+ * start-up, library callbacks where an allocation and its implicit
+ * synchronisation are not allowed.  One call creates, runs `steps` records of
+ * every chain and reads back, for ONE dense instance, allocating nothing: all
+ * working memory (chain states, fields, descriptors, validation words) lives
+ * in one file-scope device array of PNS_STATIC_SCRATCH_BYTES.
+ *   - prob: dense, n a positive multiple of 32; q (16-byte aligned), b and
+ *     betas in device memory.  cfg: as for pns_create, without exchange
+ *     (swap_interval = 0); cfg->x0, when given, in device memory; the
+ *     producer warp is not used.
+ *   - outputs: states (chains x n/32 words, host or device), multiplicities
+ *     and flips (device, chains x steps, both or neither), stats (host or
+ *     device, chains entries); any may be NULL.
+ *   - results equal pns_create + pns_run + pns_read on the same inputs.
+ *   - sizes whose working memory exceeds the array return PNS_ERR_RANGE with
+ *     the bytes needed; no partial work is done.
+ *   - the first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - every call shares the array and leaves its contents behind; each call
+ *     resets what it reads.  Calls that overlap on the GPU race on the array.
+ *   - synchronises `stream` before returning. */
+pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int64_t steps, uint32_t *states,
+                             double *multiplicities, int32_t *flips, pns_stats *stats, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

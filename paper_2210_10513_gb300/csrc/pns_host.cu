@@ -55,6 +55,8 @@ constexpr uint64_t kCkptMagic = 0x31504b4353504e50ull;  // "PNSCKP1"
 
 }  // namespace
 
+void pnsk::set_last_error(const char *msg) { g_err = msg; }
+
 struct pns_ctx {
     int device = 0;
     pns_config cfg{};

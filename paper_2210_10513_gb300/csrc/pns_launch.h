@@ -38,4 +38,7 @@ cudaError_t launch_init_fields(int fmt, int qtype, int hbytes, const InstDesc *i
                                const uint32_t *xbits, void *fields, ChainState *state, int64_t chains, int W,
                                int LD, int max_ld, cudaStream_t s);
 
+// Sets the message pns_last_error() returns on this thread.
+void set_last_error(const char *msg);
+
 }  // namespace pnsk

@@ -63,8 +63,9 @@ STATS_DTYPE = np.dtype([("steps", np.int64), ("flips", np.int64), ("stays", np.i
                         ("sum_m", np.float64), ("best_energy", np.float64)])
 assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
 
-EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore",
-           "pns_destroy", "pns_last_error")
+EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint",
+           "pns_restore", "pns_destroy", "pns_last_error", "pns_sample_static")
+STATIC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
 
@@ -86,6 +87,8 @@ def lib():
         L.pns_get_info.argtypes = [vp, vp]
         L.pns_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.pns_restore.argtypes = [vp, vp, C.c_size_t]
+        L.pns_sample_static.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, vp]
+        L.pns_sample_static.restype = C.c_int
         L.pns_destroy.argtypes = [vp]
         L.pns_destroy.restype = None
         L.pns_last_error.argtypes = []
@@ -240,6 +243,14 @@ def pns_restore(ctx, buf):
 def pns_destroy(ctx):
     if ctx:
         lib().pns_destroy(ctx)
+
+
+def pns_sample_static(problem, config, steps, states=None, multiplicities=None, flips=None, stats=None,
+                      stream=None):
+    """One dense instance, create + run + read, with no device allocation
+    (working memory is the library's fixed device array)."""
+    _check(lib().pns_sample_static(C.byref(problem), C.byref(config), int(steps), _addr(states),
+                                   _addr(multiplicities), _addr(flips), _addr(stats), _stream(stream)))
 
 
 class Sampler:

@@ -485,17 +485,29 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     }
     // A producer warp per chain pays off when the GPU is latency-bound (few
     // warps per SM); with many chains every warp already has work.
+    // Producer warps: one per 32 race numbers, plus one for the record scalars.
+    int kmax = 1;
+    for (const InstHost &ih : c->inst) kmax = std::max(kmax, ih.k);
+    const int prod_want = cfg->variant == PNS_METROPOLIS ? 1 : std::min(3, 1 + (kmax + 31) / 32);
     c->prod = 0;
     if (c->T < 32) {
         const int64_t warps = c->chains * c->T;
-        c->prod = warps <= 8ll * num_sms ? 1 : 0;
+        c->prod = warps <= 8ll * num_sms ? prod_want : 0;
     }
-    if (const char *e = getenv("PNS_PRODUCER_WARPS")) c->prod = atoi(e) > 0 && c->T < 32 ? 1 : 0;
+    if (const char *e = getenv("PNS_PRODUCER_WARPS")) c->prod = std::max(0, std::min(3, atoi(e)));
+    if (c->T + c->prod > 16 || (c->T == 32 && c->prod > 0)) c->prod = 0;
     PlanOut pl;
     int per_cta = cfg->chains_per_cta;
     if (per_cta == 0)
         if (const char *e = getenv("PNS_CHAINS_PER_CTA")) per_cta = atoi(e);
-    st = plan(*c, chains, num_sms, static_cast<size_t>(smem_optin), per_cta, pl);
+    // fewer producer warps when an exchange group or the barrier budget does
+    // not fit with them
+    while (true) {
+        pl = PlanOut();
+        st = plan(*c, chains, num_sms, static_cast<size_t>(smem_optin), per_cta, pl);
+        if (st == PNS_OK || c->prod == 0) break;
+        c->prod -= 1;
+    }
     if (st != PNS_OK) return st;
     for (int64_t i = 0; i < c->chains; ++i) chains[i].smem_off = pl.smem_off[i];
     c->n_cta = static_cast<int>(pl.cta.size());

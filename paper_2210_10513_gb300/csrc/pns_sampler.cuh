@@ -147,12 +147,41 @@ struct Mult {
     int sat;
 };
 
-__device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float beta, float anchor, float e1) {
+// Round-to-nearest-even conversion of an unsigned 64-bit integer to fp32 with
+// 32-bit integer operations only (GB300 runs 64-bit int<->float conversions on
+// its slow fp64 pipe).  Equal to __ull2float_rn for every input.
+__device__ __forceinline__ float u64_to_f32_rn(uint64_t v) {
+    const uint32_t hi = static_cast<uint32_t>(v >> 32);
+    const uint32_t lo = static_cast<uint32_t>(v);
+    if (hi == 0u && lo < (1u << 24)) return __uint2float_rn(lo);  // exact
+    const int bits = hi ? 64 - __clz(static_cast<int>(hi)) : 32 - __clz(static_cast<int>(lo));
+    const int sh = bits - 24;  // bits dropped, 1..40
+    uint32_t m;
+    bool round_up;
+    if (sh < 32) {
+        m = static_cast<uint32_t>(v >> sh);
+        const uint32_t rem = static_cast<uint32_t>(v) & ((1u << sh) - 1u);
+        const uint32_t half = 1u << (sh - 1);
+        round_up = rem > half || (rem == half && (m & 1u));
+    } else {
+        m = hi >> (sh - 32);
+        const uint32_t remh = hi & ((1u << (sh - 32)) - 1u);  // bits of hi below m
+        const uint32_t halfh = sh == 32 ? 0u : 1u << (sh - 33);
+        // the dropped part is remh * 2^32 + lo; half is 2^(sh-1)
+        if (sh == 32) round_up = lo > 0x80000000u || (lo == 0x80000000u && (m & 1u));
+        else round_up = remh > halfh || (remh == halfh && (lo > 0u || (m & 1u)));
+    }
+    if (round_up) m += 1u;  // m <= 2^24, exact in fp32
+    return __fmul_rn(__uint2float_rn(m), pow2f(sh));
+}
+
+// anchor_f = e^{-beta A} (1 when A = 0), computed by the caller as soon as the
+// anchor is known.
+__device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anchor_f, float e1) {
     Mult r;
-    float ps = __fmul_rn(__ull2float_rn(S), 0x1p-32f);
+    float ps = __fmul_rn(u64_to_f32_rn(S), 0x1p-32f);
     ps = __fdiv_rn(ps, __int2float_rn(k));
-    const float f = anchor > 0.0f ? det_expf(-__fmul_rn(beta, anchor)) : 1.0f;
-    const float p = __fmul_rn(ps, f);
+    const float p = __fmul_rn(ps, anchor_f);
     r.sat = 0;
     if (p >= 1.0f) {
         r.mi = 1;
@@ -299,27 +328,25 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
     sync_all();
 
     // ---- producer: state-independent draws for record `step` into slot `s` --
+    // Race numbers go one per lane over the first max(1, prod - 1) producer
+    // warps; the last producer warp draws the record scalars (and Basic's
+    // subset), so the two kinds of work do not diverge inside one warp.
     auto produce = [&](int s, uint64_t step) {
         unsigned char *slot = base + L.slots + s * L.slot_bytes;
         float *ex = reinterpret_cast<float *>(slot + 16);
         const int ptid = tid - TCC;
-        const int pthreads = 32 * prod;
-        const int blocks = (k + 3) >> 2;
-        for (int b = ptid; b < blocks; b += pthreads) {
-            const uint4 w = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(b));
-            const int t = 4 * b;
-            ex[t] = race_exp(w.x);
-            if (t + 1 < k) ex[t + 1] = race_exp(w.y);
-            if (t + 2 < k) ex[t + 2] = race_exp(w.z);
-            if (t + 3 < k) ex[t + 3] = race_exp(w.w);
+        const int race_warps = prod > 1 ? prod - 1 : 1;
+        if (ptid < 32 * race_warps) {
+            for (int t = ptid; t < k; t += 32 * race_warps)
+                ex[t] = race_exp(rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t)));
         }
-        if (ptid == pthreads - 1) {
+        if (wit == TC + prod - 1 && lane == 0) {
             const RecordDraws d = record_draws(seed, chain_id, step, n);
             reinterpret_cast<float *>(slot)[0] = d.e1;
             reinterpret_cast<int32_t *>(slot)[1] = d.mi;
             reinterpret_cast<float *>(slot)[2] = d.mlu;
         }
-        if (slot_list && wit == TC) {
+        if (slot_list && wit == TC + prod - 1) {
             int32_t *sl = reinterpret_cast<int32_t *>(slot + 16 + 4 * k);
             const bool ok = draw_subset_warp(seed, chain_id, step, n, k, ld, sl, bitmap, lane);
             if (lane == 0) reinterpret_cast<int32_t *>(slot)[3] = ok ? 0 : 1;
@@ -550,11 +577,16 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             const D amin = A::unkey(amin_k);
             // a4: weights, race, quantised sum
             uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
+            // e^{-beta A} for the multiplicity, independent of the visits below
+            const float af = A::tof(amin);
+            const float anchor_f = af > 0.0f ? det_expf(-__fmul_rn(beta, af)) : 1.0f;
             auto visit = [&](int t, D dv) {
                 const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dv), amin)));
-                const uint64_t qw = __float2ull_rz(__fmul_rn(w, 0x1p32f));
-                sa += static_cast<uint32_t>(qw >> 16);
-                sb += static_cast<uint32_t>(qw & 0xFFFFull);
+                // floor(w 2^32) as (floor(w 2^16), next 16 bits), all exact in fp32
+                const float ws = __fmul_rn(w, 65536.0f);
+                const float wa = truncf(ws);
+                sa += __float2uint_rz(wa);
+                sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
                 const uint32_t kb = __float_as_uint(__fdiv_rn(ex_of(t, step), w));
                 if (kb < bkey) {  // t ascending per thread: the first minimum is kept
                     bkey = kb;
@@ -604,7 +636,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             const bool always_move = variant != VAR_UNBIASED;
             if (always_move) prefetch_row(j);
             // a5: multiplicity and budget
-            const Mult mu = multiplicity_e1(S, k, beta, A::tof(amin), rd.e1);
+            const Mult mu = multiplicity_e1(S, k, anchor_f, rd.e1);
             double m = mu.md;
             const int sat = mu.sat;
             const D dj = delta_of(j);

@@ -61,6 +61,7 @@ struct pns_ctx {
     int device = 0;
     pns_config cfg{};
     int fmt = 0, qtype = 0, is_float = 0, hbytes = 4, T = 1, prod = 0;
+    int spec = 0;  // > 0: speculative kernel with this many warps (records) per chain
     std::vector<InstHost> inst;
     int32_t max_ld = 32, LD = 32, W = 1;
     int64_t chains = 0;
@@ -181,7 +182,8 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     // named barriers per CTA (ids 1..15): two per team when a team has more
     // than one warp, then one per exchange group
     const bool team_bars = TT > 32;
-    const int teams_cap = T == 32 ? 1 : std::min(512 / TT, team_bars ? 7 : 16);
+    int teams_cap = T == 32 ? 1 : std::min(512 / TT, team_bars ? 7 : 16);
+    if (c.spec > 0) teams_cap = std::max(1, std::min(512 / (32 * c.spec), 15));
     struct Unit {
         int32_t first, count, bytes;
     };
@@ -189,7 +191,8 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     const int R = pt ? c.R : 1;
     for (int64_t i = 0; i < c.chains; i += R) {
         const InstHost &ih = c.inst[chains[i].inst];
-        const int32_t per = chain_smem(ih.ld, ih.k, c.hbytes, list, c.prod > 0, slot_list).total;
+        const int32_t per = c.spec > 0 ? spec_chain_bytes(ih.ld, ih.k, c.hbytes, list, c.spec)
+                                       : chain_smem(ih.ld, ih.k, c.hbytes, list, c.prod > 0, slot_list).total;
         units.push_back({static_cast<int32_t>(i), R, per * R});
     }
     if (R > teams_cap) return fail(PNS_ERR_UNSUPPORTED, "exchange group of %d chains exceeds %d teams per CTA", R, teams_cap);
@@ -234,9 +237,9 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     close();
     int max_teams = 0;
     for (const CtaDesc &d : out.cta) max_teams = std::max(max_teams, static_cast<int>(d.count));
-    out.block = max_teams * TT;
+    out.block = max_teams * (c.spec > 0 ? 32 * c.spec : TT);
     for (const CtaDesc &d : out.cta) {
-        const int ids = (team_bars ? 2 * d.count : 0) + (pt ? d.groups : 0);
+        const int ids = c.spec > 0 ? d.count : (team_bars ? 2 * d.count : 0) + (pt ? d.groups : 0);
         if (ids > 15) return fail(PNS_ERR_UNSUPPORTED, "a CTA needs %d named barriers (15 available)", ids);
     }
     return PNS_OK;
@@ -273,7 +276,7 @@ pns_status pns_get_info(const pns_ctx *ctx, pns_info *info) {
     info->field_bytes = ctx->hbytes;
     info->field_is_float = ctx->is_float;
     info->tape_capacity = ctx->tape_cap;
-    info->warps_per_chain = ctx->T;
+    info->warps_per_chain = ctx->spec > 0 ? ctx->spec : ctx->T + ctx->prod;
     info->ctas = ctx->n_cta;
     return PNS_OK;
 }
@@ -500,6 +503,24 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     int per_cta = cfg->chains_per_cta;
     if (per_cta == 0)
         if (const char *e = getenv("PNS_CHAINS_PER_CTA")) per_cta = atoi(e);
+    // Speculative evaluation (Unbiased / Metropolis, dense, no exchange): a
+    // stay leaves the state unchanged, so D warps evaluate D future records at
+    // once.  Used when the GPU would otherwise be latency-bound.
+    c->spec = 0;
+    if (c->fmt == PNS_DENSE && cfg->swap_interval == 0 && cfg->L0 < (1ll << 31) &&
+        (cfg->variant == PNS_UNBIASED || cfg->variant == PNS_METROPOLIS) && kmax <= 128 &&
+        cfg->warps_per_chain == 0) {
+        if (c->chains * 8 <= 16ll * num_sms) c->spec = 8;
+        else if (c->chains * 4 <= 16ll * num_sms) c->spec = 4;
+    }
+    if (const char *e = getenv("PNS_SPEC_DEPTH")) {
+        const int d = atoi(e);
+        c->spec = (d == 0 || spec_supported(c->qtype, d)) ? d : 0;
+    }
+    if (c->spec > 0 && !(c->fmt == PNS_DENSE && cfg->swap_interval == 0 && cfg->L0 < (1ll << 31) &&
+                         (cfg->variant == PNS_UNBIASED || cfg->variant == PNS_METROPOLIS)))
+        c->spec = 0;
+    if (c->spec > 0) c->prod = 0;
     // fewer producer warps when an exchange group or the barrier budget does
     // not fit with them
     while (true) {
@@ -611,12 +632,16 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.pt = pt ? 1 : 0;
     P.tape = c->cfg.tape;
     P.prod = c->prod;
+    auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {
+        if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->block, c->smem, s);
+        return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->block, c->smem, s);
+    };
     if (!plain) {
-        CU(launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, P, c->n_cta, c->block, c->smem, s));
+        CU(launch(P, c->n_cta));
     } else {
         for (int b = 0; b < c->n_cta; ++b) {
             P.cta = c->d_cta + b;
-            CU(launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, P, 1, c->block, c->smem, s));
+            CU(launch(P, 1));
         }
     }
     return PNS_OK;

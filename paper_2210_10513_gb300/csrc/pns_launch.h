@@ -38,6 +38,12 @@ cudaError_t launch_init_fields(int fmt, int qtype, int hbytes, const InstDesc *i
                                const uint32_t *xbits, void *fields, ChainState *state, int64_t chains, int W,
                                int LD, int max_ld, cudaStream_t s);
 
+// Speculative kernel for Unbiased PNS / Metropolis on dense Q: D warps per
+// chain, warp w evaluates record step + w assuming the earlier ones stay.
+bool spec_supported(int qtype, int D);
+cudaError_t launch_spec(int qtype, int D, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
+int32_t spec_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, bool list, int32_t D);
+
 // Sets the message pns_last_error() returns on this thread.
 void set_last_error(const char *msg);
 

@@ -126,12 +126,13 @@ struct RecordDraws {
     float mlu;     // Metropolis log-uniform (STEP word 3)
 };
 
-__device__ __forceinline__ RecordDraws record_draws(uint64_t seed, uint32_t chain, uint64_t step, int n) {
+__device__ __forceinline__ RecordDraws record_draws(uint64_t seed, uint32_t chain, uint64_t step, int n,
+                                                    bool metropolis = true, bool race = true) {
     const uint4 w = rng_block(seed, TAG_STEP, chain, step, 0);
     RecordDraws d;
-    d.e1 = -det_logf(u01_fine64((static_cast<uint64_t>(w.y) << 32) | static_cast<uint64_t>(w.x)));
+    d.e1 = race ? -det_logf(u01_fine64((static_cast<uint64_t>(w.y) << 32) | static_cast<uint64_t>(w.x))) : 0.0f;
     d.mi = static_cast<int32_t>(__umulhi(w.z, static_cast<uint32_t>(n)));
-    d.mlu = det_logf(u01_grid(w.w));
+    d.mlu = metropolis ? det_logf(u01_grid(w.w)) : 0.0f;
     return d;
 }
 

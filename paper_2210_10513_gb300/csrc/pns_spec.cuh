@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
             res.dj = 0;
             res.m = 0.0;
             res.pad = 0;
-            const RecordDraws rd = record_draws(seed, chain_id, step, n);
+            const bool met = variant == VAR_METROPOLIS;
+            const RecordDraws rd = record_draws(seed, chain_id, step, n, met, !met);
             if (variant == VAR_METROPOLIS) {
                 const D_t d = delta_of(rd.mi);
                 const float y = -__fmul_rn(beta, A::tof(d));
@@ -169,11 +170,15 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 uint32_t lmin = 0xFFFFFFFFu;
                 D_t dl[CPT];
                 const bool fast = k <= 32 * CPT;
+                // fast path: lane handles cpl consecutive positions, so one
+                // Philox block (four words) serves up to four of them
+                const int cpl = (k + 31) >> 5;
+                const int t0 = lane * cpl;
                 if (fast) {
 #pragma unroll
                     for (int u = 0; u < CPT; ++u) {
-                        const int t = lane + 32 * u;
-                        if (t < k) {
+                        const int t = t0 + u;
+                        if (u < cpl && t < k) {
                             dl[u] = delta_of(cand(t));
                             const uint32_t kd = A::key(A::pos(dl[u]));
                             lmin = kd < lmin ? kd : lmin;
@@ -189,13 +194,13 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 const float af = A::tof(amin);
                 const float anchor_f = af > 0.0f ? det_expf(-__fmul_rn(beta, af)) : 1.0f;
                 uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
-                auto visit = [&](int t, D_t dv) {
+                auto visit = [&](int t, D_t dv, uint32_t word) {
                     const float wt = det_expf(-__fmul_rn(beta, A::diff(A::pos(dv), amin)));
                     const float ws = __fmul_rn(wt, 65536.0f);
                     const float wa = truncf(ws);
                     sa += __float2uint_rz(wa);
                     sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                    const float ex = race_exp(rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t)));
+                    const float ex = race_exp(word);
                     const uint32_t kb = __float_as_uint(__fdiv_rn(ex, wt));
                     if (kb < bkey) {
                         bkey = kb;
@@ -203,13 +208,23 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                     }
                 };
                 if (fast) {
+                    uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t0 >> 2));
+                    uint32_t cur_b = static_cast<uint32_t>(t0 >> 2);
 #pragma unroll
                     for (int u = 0; u < CPT; ++u) {
-                        const int t = lane + 32 * u;
-                        if (t < k) visit(t, dl[u]);
+                        const int t = t0 + u;
+                        if (u < cpl && t < k) {
+                            const uint32_t bt = static_cast<uint32_t>(t) >> 2;
+                            if (bt != cur_b) {
+                                blk = rng_block(seed, TAG_RACE, chain_id, step, bt);
+                                cur_b = bt;
+                            }
+                            visit(t, dl[u], pick_word(blk, static_cast<uint32_t>(t) & 3u));
+                        }
                     }
                 } else {
-                    for (int t = lane; t < k; t += 32) visit(t, delta_of(cand(t)));
+                    for (int t = lane; t < k; t += 32)
+                        visit(t, delta_of(cand(t)), rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t)));
                 }
                 const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
                 const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);

@@ -98,7 +98,8 @@ typedef struct {
     int64_t swap_interval;     /* 0: no exchange; else original samples between exchange
                                   rounds (Unbiased: a multiple of L0; Metropolis: any >= 1) */
     uint64_t seed;             /* Philox key */
-    int32_t tape;              /* 0: no per-step records; 1: record (flip, M) every step */
+    int32_t tape;              /* 0: no per-step records; 1: record (flip, M) every step;
+                                  2: also the state bits and energy at each record's start */
     int32_t warps_per_chain;   /* 0: choose automatically; else 1, 2, 4, 8, 16 or 32 */
     int32_t chains_per_cta;    /* 0: choose automatically; else at most this many chains
                                   (or exchange groups) per CTA */
@@ -163,6 +164,43 @@ pns_status pns_run_plain(pns_ctx *ctx, int64_t steps, void *stream);
  * Any pointer may be NULL.  Returns a device error latched by earlier runs. */
 pns_status pns_read(pns_ctx *ctx, uint32_t *states, double *multiplicities, int32_t *flips, pns_stats *stats,
                     void *stream);
+
+/* With cfg.tape = 2, copies the sample tape of the last run: the state bits
+ * (chains x tape_capacity x W words) and the energy (chains x tape_capacity)
+ * at the start of each record, i.e. the jump-chain state J that the record's
+ * multiplicity M weighs (Sec. 1.2, Theorem 3 (5)). */
+pns_status pns_read_samples(pns_ctx *ctx, uint32_t *states, double *energies, void *stream);
+
+/* Scalars of a multiplicity-weighted sample: weight W = sum M, <E>, Var(E),
+ * number of samples. */
+typedef struct {
+    double weight;
+    double mean_energy;
+    double var_energy;
+    double samples;
+} pns_moment_scalars;
+
+/* Multiplicity-weighted moments of the last run's records (cfg.tape = 2, no
+ * replica exchange) of the chains of one (instance, temperature index):
+ * <x> (n), <x x^T> (n x n), Cov(E, x) (n), Cov(E, x x^T) (n x n), in fp64,
+ * with <f> = sum_k M_k f(J_k) / sum_k M_k (Theorem 3 (5)).  The second moments
+ * run on tcgen05 tensor cores (bf16 bit tiles, weights split into three bf16
+ * parts, fp32 accumulation per 16384 samples, fp64 across).  n <= 64.
+ * Outputs may be host or device memory, any may be NULL. */
+pns_status pns_moments(pns_ctx *ctx, int32_t instance, int32_t beta_idx, pns_moment_scalars *scalars,
+                       double *mean_x, double *mean_xx, double *cov_ex, double *cov_exx, void *stream);
+
+/* Gradients from moments (all pointers device memory, fp64):
+ *  data_xx == NULL: of the mean energy <E>:
+ *      dQ = <x x^T> - beta Cov(E, x x^T), db = <x> - beta Cov(E, x), dbeta = -Var(E);
+ *  else: of the Boltzmann log-likelihood of data with moments data_x, data_xx
+ *  and mean energy data_mean_energy:
+ *      dQ = -beta (data_xx - <x x^T>), db = -beta (data_x - <x>), dbeta = -data_E + <E>.
+ *  `scalars` points to a device pns_moment_scalars. */
+pns_status pns_energy_grads(int32_t n, float beta, const pns_moment_scalars *scalars, const double *mean_x,
+                            const double *mean_xx, const double *cov_ex, const double *cov_exx, const double *data_x,
+                            const double *data_xx, double data_mean_energy, double *dQ, double *db, double *dbeta,
+                            void *stream);
 
 /* Copies the maintained local fields h (chains x field_stride elements of
  * field_bytes each, integers or fp32 per pns_info) to `out`. */

@@ -81,6 +81,8 @@ struct pns_ctx {
     int32_t *d_status = nullptr;
     int32_t *d_tape_flip = nullptr;
     double *d_tape_m = nullptr;
+    uint32_t *d_tape_x = nullptr;   // tape = 2
+    double *d_tape_E = nullptr;
     int64_t tape_alloc = 0;  // records per chain allocated
     int64_t tape_cap = 0;    // records per chain of the last run
     // plan
@@ -95,7 +97,7 @@ void free_ctx(pns_ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->d_q, c->d_rowptr, c->d_col, c->d_diag, c->d_b, c->d_betas, c->d_inst, c->d_chain,
                     c->d_state, c->d_x, c->d_fields, c->d_cta, c->d_cta_chains, c->d_status, c->d_tape_flip,
-                    c->d_tape_m};
+                    c->d_tape_m,  c->d_tape_x, c->d_tape_E};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -110,7 +112,7 @@ pns_status check_args(const pns_problem *probs, int32_t n_probs, const pns_confi
         return fail(PNS_ERR_INVALID_ARG, "unknown subset mode %d", cfg->subset);
     if (cfg->chains_per_replica < 1) return fail(PNS_ERR_INVALID_ARG, "chains_per_replica must be >= 1");
     if (cfg->L0 < 1) return fail(PNS_ERR_INVALID_ARG, "L0 must be >= 1");
-    if (cfg->tape != 0 && cfg->tape != 1) return fail(PNS_ERR_INVALID_ARG, "tape must be 0 or 1");
+    if (cfg->tape < 0 || cfg->tape > 2) return fail(PNS_ERR_INVALID_ARG, "tape must be 0, 1 or 2");
     const int w = cfg->warps_per_chain;
     if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32))
         return fail(PNS_ERR_INVALID_ARG, "warps_per_chain must be 0, 1, 2, 4, 8, 16 or 32");
@@ -596,11 +598,19 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
         if (cap > c->tape_alloc) {
             if (c->d_tape_flip) cudaFree(c->d_tape_flip);
             if (c->d_tape_m) cudaFree(c->d_tape_m);
+            if (c->d_tape_x) cudaFree(c->d_tape_x);
+            if (c->d_tape_E) cudaFree(c->d_tape_E);
             c->d_tape_flip = nullptr;
             c->d_tape_m = nullptr;
+            c->d_tape_x = nullptr;
+            c->d_tape_E = nullptr;
             c->tape_alloc = 0;
             CU(cudaMalloc(&c->d_tape_flip, sizeof(int32_t) * cap * c->chains));
             CU(cudaMalloc(&c->d_tape_m, sizeof(double) * cap * c->chains));
+            if (c->cfg.tape == 2) {
+                CU(cudaMalloc(&c->d_tape_x, sizeof(uint32_t) * c->W * cap * c->chains));
+                CU(cudaMalloc(&c->d_tape_E, sizeof(double) * cap * c->chains));
+            }
             c->tape_alloc = cap;
         }
         c->tape_cap = cap;
@@ -618,6 +628,8 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.fields = c->d_fields;
     P.tape_flip = c->d_tape_flip;
     P.tape_m = c->d_tape_m;
+    P.tape_x = c->d_tape_x;
+    P.tape_E = c->d_tape_E;
     P.status = c->d_status;
     P.tape_cap = c->tape_cap;
     P.steps = steps;
@@ -696,6 +708,85 @@ pns_status pns_read(pns_ctx *c, uint32_t *states, double *mult, int32_t *flips, 
         }
     }
     CU(cudaStreamSynchronize(s));
+    return PNS_OK;
+}
+
+pns_status pns_read_samples(pns_ctx *c, uint32_t *states, double *energies, void *stream) {
+    if (!c) return fail(PNS_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->cfg.tape != 2 || !c->d_tape_x) return fail(PNS_ERR_STATE, "no sample tape (needs tape = 2 and a run)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pns_status st = sync_and_check(c, s);
+    if (st != PNS_OK) return st;
+    if (states)
+        CU(cudaMemcpyAsync(states, c->d_tape_x, sizeof(uint32_t) * c->W * c->tape_cap * c->chains,
+                           cudaMemcpyDefault, s));
+    if (energies)
+        CU(cudaMemcpyAsync(energies, c->d_tape_E, sizeof(double) * c->tape_cap * c->chains, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    return PNS_OK;
+}
+
+pns_status pns_moments(pns_ctx *c, int32_t instance, int32_t beta_idx, pns_moment_scalars *scalars, double *mean_x,
+                       double *mean_xx, double *cov_ex, double *cov_exx, void *stream) {
+    if (!c) return fail(PNS_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->cfg.tape != 2 || !c->d_tape_x) return fail(PNS_ERR_STATE, "no sample tape (needs tape = 2 and a run)");
+    if (c->cfg.swap_interval != 0) return fail(PNS_ERR_UNSUPPORTED, "moments need a run without replica exchange");
+    if (instance < 0 || instance >= static_cast<int32_t>(c->inst.size()))
+        return fail(PNS_ERR_INVALID_ARG, "instance out of range");
+    const InstHost &ih = c->inst[instance];
+    if (beta_idx < 0 || beta_idx >= ih.R) return fail(PNS_ERR_INVALID_ARG, "beta_idx out of range");
+    if (ih.n > 64) return fail(PNS_ERR_UNSUPPORTED, "moments support n <= 64");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pns_status st = sync_and_check(c, s);
+    if (st != PNS_OK) return st;
+    // chains of (instance, slot = beta_idx); without exchange slot == temperature
+    std::vector<int32_t> ids;
+    int64_t base = 0;
+    for (int p = 0; p < instance; ++p) base += static_cast<int64_t>(c->cfg.chains_per_replica) * c->inst[p].R;
+    for (int r = 0; r < c->cfg.chains_per_replica; ++r) ids.push_back(static_cast<int32_t>(base + r * ih.R + beta_idx));
+    const int64_t recs = c->tape_cap;
+    const int n = ih.n;
+    const size_t scratch_bytes = moments_scratch_bytes(recs * static_cast<int64_t>(ids.size()), n);
+    int32_t *d_ids = nullptr;
+    void *d_scratch = nullptr;
+    double *d_out = nullptr;
+    struct Free {
+        void **a, **b, **c;
+        ~Free() {
+            if (*a) cudaFree(*a);
+            if (*b) cudaFree(*b);
+            if (*c) cudaFree(*c);
+        }
+    } fr{reinterpret_cast<void **>(&d_ids), &d_scratch, reinterpret_cast<void **>(&d_out)};
+    CU(cudaMalloc(&d_ids, sizeof(int32_t) * ids.size()));
+    CU(cudaMalloc(&d_scratch, scratch_bytes));
+    const size_t out_elems = 4 + 2 * static_cast<size_t>(n) + 2 * static_cast<size_t>(n) * n;
+    CU(cudaMalloc(&d_out, sizeof(double) * out_elems));
+    CU(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, s));
+    double *o_sc = d_out, *o_x = d_out + 4, *o_xx = o_x + n, *o_ex = o_xx + n * n, *o_exx = o_ex + n;
+    CU(launch_moments(c->d_tape_x, c->d_tape_m, c->d_tape_E, d_ids, static_cast<int64_t>(ids.size()), c->tape_cap,
+                      recs, c->W, n, d_scratch, c->d_status, o_sc, o_x, o_xx, o_ex, o_exx, s));
+    st = sync_and_check(c, s);
+    if (st != PNS_OK) return st;
+    if (scalars) CU(cudaMemcpyAsync(scalars, o_sc, sizeof(double) * 4, cudaMemcpyDefault, s));
+    if (mean_x) CU(cudaMemcpyAsync(mean_x, o_x, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (mean_xx) CU(cudaMemcpyAsync(mean_xx, o_xx, sizeof(double) * n * n, cudaMemcpyDefault, s));
+    if (cov_ex) CU(cudaMemcpyAsync(cov_ex, o_ex, sizeof(double) * n, cudaMemcpyDefault, s));
+    if (cov_exx) CU(cudaMemcpyAsync(cov_exx, o_exx, sizeof(double) * n * n, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    return PNS_OK;
+}
+
+pns_status pns_energy_grads(int32_t n, float beta, const pns_moment_scalars *scalars, const double *mean_x,
+                            const double *mean_xx, const double *cov_ex, const double *cov_exx, const double *data_x,
+                            const double *data_xx, double data_mean_energy, double *dQ, double *db, double *dbeta,
+                            void *stream) {
+    if (n < 1 || !scalars || !mean_x || !mean_xx || !dQ || !db || !dbeta)
+        return fail(PNS_ERR_INVALID_ARG, "missing argument");
+    if (!data_xx && (!cov_ex || !cov_exx)) return fail(PNS_ERR_INVALID_ARG, "mean-energy gradients need covariances");
+    if (data_xx && !data_x) return fail(PNS_ERR_INVALID_ARG, "data_x is required with data_xx");
+    CU(launch_grads(n, beta, reinterpret_cast<const double *>(scalars), mean_x, mean_xx, cov_ex, cov_exx, data_x,
+                    data_xx, data_mean_energy, dQ, db, dbeta, static_cast<cudaStream_t>(stream)));
     return PNS_OK;
 }
 

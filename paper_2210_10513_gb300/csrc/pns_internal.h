@@ -71,6 +71,8 @@ struct KParams {
     void *fields;           // chain c at c * LD elements
     int32_t *tape_flip;     // chain c at c * tape_cap
     double *tape_m;
+    uint32_t *tape_x;       // tape = 2: state bits at each record's start, W words per record
+    double *tape_E;         // tape = 2: energy at each record's start
     int32_t *status;        // device status word (first error wins)
     int64_t tape_cap;
     int64_t steps;          // records (no exchange) or original samples (exchange)

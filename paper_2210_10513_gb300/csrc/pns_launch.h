@@ -44,6 +44,17 @@ bool spec_supported(int qtype, int D);
 cudaError_t launch_spec(int qtype, int D, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
 int32_t spec_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, bool list, int32_t D);
 
+// Multiplicity-weighted moments of tape = 2 samples (n <= 64) on tcgen05
+// tensor cores, and gradients assembled from them.
+size_t moments_scratch_bytes(int64_t samples, int n);
+cudaError_t launch_moments(const uint32_t *tape_x, const double *tape_m, const double *tape_E,
+                           const int32_t *chain_ids, int64_t chains, int64_t cap, int64_t recs, int W, int n,
+                           void *scratch, int32_t *status, double *scalars, double *mean_x, double *mean_xx,
+                           double *cov_ex, double *cov_exx, cudaStream_t s);
+cudaError_t launch_grads(int n, float beta, const double *scalars, const double *mean_x, const double *mean_xx,
+                         const double *cov_ex, const double *cov_exx, const double *data_x, const double *data_xx,
+                         double data_E, double *dQ, double *db, double *dbeta, cudaStream_t s);
+
 // Sets the message pns_last_error() returns on this thread.
 void set_last_error(const char *msg);
 

@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
     bool pend = false;
     auto flush_record = [&]() {
         if (pend) {
-            if (ctid == 0 && P.tape && tape_pos < P.tape_cap) {
+            if (ctid == 0 && P.tape >= 1 && tape_pos < P.tape_cap) {
                 const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos;
                 P.tape_flip[o] = pend_flip;
                 P.tape_m[o] = pend_m;
@@ -487,8 +487,22 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
         return race_exp(rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t)));
     };
 
+    // tape = 2: the state a record starts from (the jump-chain sample J that
+    // its multiplicity weighs) and its energy
+    int64_t rec_started = 0;
+    auto sample_record = [&]() {
+        if (P.tape == 2 && rec_started < P.tape_cap) {
+            const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + rec_started;
+            uint32_t *tx = P.tape_x + o * P.W;
+            for (int q = ctid; q < P.W; q += TCC) tx[q] = q < ld / 32 ? xw[q] : 0u;
+            if (ctid == 0) P.tape_E[o] = st.E;
+        }
+        rec_started += 1;
+    };
+
     // One record.  Returns true when the record was an Unbiased period end.
     auto one_record = [&]() -> bool {
+        sample_record();
         const uint64_t step = static_cast<uint64_t>(st.step);
         const unsigned char *slot = base + L.slots + cur * L.slot_bytes;
         RecordDraws rd;

@@ -256,6 +256,17 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 break;
             }
         const int ncommit = first < Dr ? first + 1 : Dr;
+        if (P.tape == 2) {
+            // every committed record starts from the current state
+            for (int idx = tid; idx < ncommit * P.W; idx += TT) {
+                const int q = idx / P.W, wd = idx - q * P.W;
+                if (tape_pos + q < P.tape_cap) {
+                    const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos + q;
+                    P.tape_x[o * P.W + wd] = wd < ld / 32 ? xw[wd] : 0u;
+                    if (wd == 0) P.tape_E[o] = st.E;
+                }
+            }
+        }
         if (w < ncommit && lane == 0 && P.tape && tape_pos + w < P.tape_cap) {
             const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos + w;
             const bool mv = w == first;

@@ -50,6 +50,11 @@ class pns_info(C.Structure):
                 ("warps_per_chain", C.c_int32), ("ctas", C.c_int32)]
 
 
+class pns_moment_scalars(C.Structure):
+    _fields_ = [("weight", C.c_double), ("mean_energy", C.c_double), ("var_energy", C.c_double),
+                ("samples", C.c_double)]
+
+
 class pns_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("flips", C.c_int64), ("stays", C.c_int64), ("saturated", C.c_int64),
                 ("swaps_accepted", C.c_int64), ("budget_left", C.c_int64), ("tape_records", C.c_int64),
@@ -63,8 +68,9 @@ STATS_DTYPE = np.dtype([("steps", np.int64), ("flips", np.int64), ("stays", np.i
                         ("sum_m", np.float64), ("best_energy", np.float64)])
 assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
 
-EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_fields", "pns_get_info", "pns_checkpoint",
-           "pns_restore", "pns_destroy", "pns_last_error", "pns_sample_static")
+EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_read_samples", "pns_moments",
+           "pns_energy_grads", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore", "pns_destroy",
+           "pns_last_error", "pns_sample_static")
 STATIC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
@@ -87,6 +93,12 @@ def lib():
         L.pns_get_info.argtypes = [vp, vp]
         L.pns_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.pns_restore.argtypes = [vp, vp, C.c_size_t]
+        L.pns_read_samples.argtypes = [vp, vp, vp, vp]
+        L.pns_read_samples.restype = C.c_int
+        L.pns_moments.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp]
+        L.pns_moments.restype = C.c_int
+        L.pns_energy_grads.argtypes = [C.c_int32, C.c_float, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp]
+        L.pns_energy_grads.restype = C.c_int
         L.pns_sample_static.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, vp]
         L.pns_sample_static.restype = C.c_int
         L.pns_destroy.argtypes = [vp]
@@ -191,7 +203,7 @@ def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica
     c.L0 = int(L0)
     c.swap_interval = int(swap_interval)
     c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
-    c.tape = int(bool(tape))
+    c.tape = int(tape)
     c.warps_per_chain = int(warps_per_chain)
     c.chains_per_cta = int(chains_per_cta)
     c.x0 = _addr(x0)
@@ -221,6 +233,23 @@ def pns_get_info(ctx):
 
 def pns_read(ctx, states=None, multiplicities=None, flips=None, stats=None, stream=None):
     _check(lib().pns_read(ctx, _addr(states), _addr(multiplicities), _addr(flips), _addr(stats), _stream(stream)))
+
+
+def pns_read_samples(ctx, states=None, energies=None, stream=None):
+    _check(lib().pns_read_samples(ctx, _addr(states), _addr(energies), _stream(stream)))
+
+
+def pns_moments(ctx, instance, beta_idx, scalars=None, mean_x=None, mean_xx=None, cov_ex=None, cov_exx=None,
+                stream=None):
+    _check(lib().pns_moments(ctx, int(instance), int(beta_idx), _addr(scalars), _addr(mean_x), _addr(mean_xx),
+                             _addr(cov_ex), _addr(cov_exx), _stream(stream)))
+
+
+def pns_energy_grads(n, beta, scalars, mean_x, mean_xx, cov_ex, cov_exx, data_x, data_xx, data_mean_energy, dQ, db,
+                     dbeta, stream=None):
+    _check(lib().pns_energy_grads(int(n), C.c_float(beta), _addr(scalars), _addr(mean_x), _addr(mean_xx),
+                                  _addr(cov_ex), _addr(cov_exx), _addr(data_x), _addr(data_xx),
+                                  float(data_mean_energy), _addr(dQ), _addr(db), _addr(dbeta), _stream(stream)))
 
 
 def pns_fields(ctx, out, stream=None):
@@ -288,6 +317,29 @@ class Sampler:
             f = np.empty((C_, info.tape_capacity), dtype=np.int32)
         pns_read(self.ctx, states, m, f, stats, stream)
         return dict(states=states, stats=stats, m=m, flips=f)
+
+    def samples(self, stream=None):
+        """State bits (chains x capacity x W) and energies at each record's start (tape = 2)."""
+        info = pns_get_info(self.ctx)
+        x = np.empty((info.chains, info.tape_capacity, info.words_per_chain), dtype=np.uint32)
+        e = np.empty((info.chains, info.tape_capacity), dtype=np.float64)
+        pns_read_samples(self.ctx, x, e, stream)
+        return x, e
+
+    def moments(self, n, instance=0, beta_idx=0, stream=None, device=None):
+        """Multiplicity-weighted moments (fp64): scalars [W, <E>, Var E, samples],
+        <x>, <x x^T>, Cov(E, x), Cov(E, x x^T).  numpy on the host, or torch
+        tensors on `device`."""
+        if device is None:
+            out = dict(scalars=np.empty(4), mean_x=np.empty(n), mean_xx=np.empty((n, n)), cov_ex=np.empty(n),
+                       cov_exx=np.empty((n, n)))
+        else:
+            import torch
+            f = lambda *shape: torch.empty(shape, dtype=torch.float64, device=device)  # noqa: E731
+            out = dict(scalars=f(4), mean_x=f(n), mean_xx=f(n, n), cov_ex=f(n), cov_exx=f(n, n))
+        pns_moments(self.ctx, instance, beta_idx, out["scalars"], out["mean_x"], out["mean_xx"], out["cov_ex"],
+                    out["cov_exx"], stream)
+        return out
 
     def fields(self, stream=None):
         info = pns_get_info(self.ctx)

@@ -341,6 +341,62 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def fit_workload(args):
+    """Differentiation: n = 64 fp32 QUBO, Q = (A + A^T)/2 with A N(0, 0.1^2),
+    b N(0, 0.1^2), beta = 1, 8192 chains, Unbiased k = 16, L0 = 100.  One step
+    = one forward (the sampler for `--records` records per chain with the
+    sample tape) + the tensor-core moments + the gradient kernel."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    wl = synth.workload_fit(64, seed=args.seed)
+    n = 64
+    chains = 8192
+    recs = args.records
+    s = pns.Sampler([dict(n=n, q=torch.from_numpy(wl["q"]).to(dev), b=torch.from_numpy(wl["b"]).to(dev),
+                          betas=[1.0])], variant="unbiased", k=16, chains_per_replica=chains, L0=100, seed=args.seed,
+                    tape=2)
+    s.run(recs)  # burn-in
+    f64 = lambda *shape: torch.empty(shape, dtype=torch.float64, device=dev)  # noqa: E731
+    mom = dict(scalars=f64(4), mean_x=f64(n), mean_xx=f64(n, n), cov_ex=f64(n), cov_exx=f64(n, n))
+    dQ, db, dbeta = f64(n, n), f64(n), f64(1)
+    t_samp, t_mom = [], []
+    for it in range(args.warmup + args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        s.run(recs)
+        e1.record(stream)
+        pns.pns_moments(s.ctx, 0, 0, mom["scalars"], mom["mean_x"], mom["mean_xx"], mom["cov_ex"], mom["cov_exx"])
+        pns.pns_energy_grads(n, 1.0, mom["scalars"], mom["mean_x"], mom["mean_xx"], mom["cov_ex"], mom["cov_exx"],
+                             None, None, 0.0, dQ, db, dbeta)
+        e2.record(stream)
+        e2.synchronize()
+        if it >= args.warmup:
+            t_samp.append(e0.elapsed_time(e1))
+            t_mom.append(e1.elapsed_time(e2))
+    samples = float(chains) * recs
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    mma_flops = samples * 2 * 128 * 64 * 3  # three M = 128, N = 64 MMAs per sample (padded planes)
+    tape_bytes = samples * (8 + 8 + 8)  # bits (2 words), M, E read by the moments kernels
+    ms_s = float(np.mean(t_samp))
+    ms_m = float(np.mean(t_mom))
+    line = {"metric": "forward+backward samples/s", "workload": "fit", "value": samples / ((ms_s + ms_m) / 1e3),
+            "unit": "samples/s", "forward_ms": ms_s, "moments_and_grads_ms": ms_m,
+            "forward_records_per_s": samples / (ms_s / 1e3),
+            "moments_mma_tflops": mma_flops / (ms_m / 1e3) / 1e12, "bf16_peak_tflops": bf16,
+            "moments_tape_GBs": tape_bytes / (ms_m / 1e3) / 1e9, "mean_energy": float(mom["scalars"][1].item()),
+            "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "fit: n=64 fp32, 8192 chains, Unbiased k=16, beta=1, %d records per chain per step, "
+                                   "moments on tcgen05 + gradients" % recs}}
+    s.close()
+    print(json.dumps(line), flush=True)
+
+
 def side_workload(args):
     """Other benchmark shapes, one JSON line each (not the headline):
     tempering -- 512 fp32 instances, n uniform in [128, 2048], 8 replicas on a
@@ -369,6 +425,8 @@ def side_workload(args):
         row_bytes = 4 * ns
         desc = ("tempering: %d fp32 instances n~U[128,2048], 8 replicas (beta 0.1..10), Unbiased k=n/16, "
                 "swap every 100 original samples, 1000 original samples per chain per step" % n_inst)
+    elif args.workload == "fit":
+        return fit_workload(args)
     else:
         side = 256
         csr = synth.lattice_csr(side, seed=args.seed)
@@ -426,7 +484,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the Basic / plain side measurements")
-    ap.add_argument("--workload", default="dense1024", choices=["dense1024", "tempering", "lattice"])
+    ap.add_argument("--workload", default="dense1024", choices=["dense1024", "tempering", "lattice", "fit"])
     ap.add_argument("--instances", type=int, default=512)
     args = ap.parse_args()
     if args.workload != "dense1024":

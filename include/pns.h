@@ -103,9 +103,12 @@ typedef struct {
     int32_t warps_per_chain;   /* 0: choose automatically; else 1, 2, 4, 8, 16 or 32 */
     int32_t chains_per_cta;    /* 0: choose automatically; else at most this many chains
                                   (or exchange groups) per CTA */
-    int32_t reserved;          /* must be 0 */
+    int32_t chain_base;        /* global id of this context's first chain, >= 0: a shard of a larger
+                                  job draws the same Philox streams as the whole job would */
     const uint32_t *x0;        /* NULL (all zeros) or initial bit-packed states: chain c,
                                   bit i at word c*W + i/32, bit i%32; W = pns_info.words_per_chain */
+    int32_t group_base;        /* global id of this context's first exchange group, >= 0 */
+    int32_t reserved;          /* must be 0 */
 } pns_config;
 
 /* Chain numbering: instance p, chain r of each temperature, replica slot s:

@@ -277,13 +277,16 @@ def chain_layout(n_replicas, chains_per_replica):
             gid += 1
 
 
-def run_independent(problems, betas, cfg_kwargs, chains_per_replica, x0, n_records, chain_ids=None, tape=True):
+def run_independent(problems, betas, cfg_kwargs, chains_per_replica, x0, n_records, chain_ids=None, tape=True,
+                    id_base=0):
     """Run every chain (or the listed chain ids) independently for n_records
     records.  x0: dict chain_id -> bits (uint8[n]) or None for all-zero.
+    Chain ids start at `id_base` (a shard of a larger job).
     Returns dict chain_id -> result dict."""
     cfg = make_config(**cfg_kwargs)
     out = {}
-    layout = list(chain_layout([len(b) for b in betas], chains_per_replica))
+    layout = [(p, c, r, cid + id_base, gid) for p, c, r, cid, gid in
+              chain_layout([len(b) for b in betas], chains_per_replica)]
     want = None if chain_ids is None else set(int(c) for c in chain_ids)
     for p, c, r, cid, gid in layout:
         if want is not None and cid not in want:

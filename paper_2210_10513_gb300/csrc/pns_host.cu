@@ -117,8 +117,8 @@ pns_status check_args(const pns_problem *probs, int32_t n_probs, const pns_confi
     if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32))
         return fail(PNS_ERR_INVALID_ARG, "warps_per_chain must be 0, 1, 2, 4, 8, 16 or 32");
     if (cfg->swap_interval < 0) return fail(PNS_ERR_INVALID_ARG, "swap_interval must be >= 0");
-    if (cfg->chains_per_cta < 0 || cfg->reserved != 0)
-        return fail(PNS_ERR_INVALID_ARG, "chains_per_cta must be >= 0 and reserved 0");
+    if (cfg->chains_per_cta < 0 || cfg->reserved != 0 || cfg->chain_base < 0 || cfg->group_base < 0)
+        return fail(PNS_ERR_INVALID_ARG, "chains_per_cta, chain_base, group_base must be >= 0 and reserved 0");
     if (cfg->swap_interval > 0) {
         if (cfg->variant != PNS_UNBIASED && cfg->variant != PNS_METROPOLIS)
             return fail(PNS_ERR_INVALID_ARG, "replica exchange needs PNS_UNBIASED or PNS_METROPOLIS");
@@ -644,6 +644,8 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.pt = pt ? 1 : 0;
     P.tape = c->cfg.tape;
     P.prod = c->prod;
+    P.chain_base = static_cast<uint32_t>(c->cfg.chain_base);
+    P.group_base = static_cast<uint32_t>(c->cfg.group_base);
     auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {
         if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->block, c->smem, s);
         return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->block, c->smem, s);

@@ -84,6 +84,8 @@ struct KParams {
     int32_t pt;             // exchange on
     int32_t tape;
     int32_t prod;           // producer warps per chain (0: consumers draw their own numbers)
+    uint32_t chain_base;    // global id of chain 0 (Philox stream id = chain_base + chain)
+    uint32_t group_base;    // global id of exchange group 0
 };
 
 PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }

@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
     }
     ChainState st = P.state[cid];
     const uint64_t seed = P.seed;
-    const uint32_t chain_id = static_cast<uint32_t>(cid);
+    const uint32_t chain_id = static_cast<uint32_t>(cid) + P.chain_base;
     sync_all();
 
     // ---- producer: state-independent draws for record `step` into slot `s` --
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                             const float db = __fsub_rn(in.betas[a], in.betas[a + 1]);
                             const float de = __double2float_rn(__dsub_rn(Ea, Eb));
                             const float xr = __fmul_rn(db, de);
-                            const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd.group), rnd,
+                            const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd.group) + P.group_base, rnd,
                                                         static_cast<uint32_t>(q));
                             if (det_logf(u01_grid(w)) < xr) {
                                 *reinterpret_cast<int32_t *>(pa + 648) = a + 1;

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
     ChainState st = P.state[cid];
     const float beta = in.betas[st.beta_idx];
     const uint64_t seed = P.seed;
-    const uint32_t chain_id = static_cast<uint32_t>(cid);
+    const uint32_t chain_id = static_cast<uint32_t>(cid) + P.chain_base;
     int cur_list = 0;          // list buffer holding the current period's set
     bool list_valid = false;
     int64_t tape_pos = 0;

@@ -273,6 +273,7 @@ pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int
     P.pt = 0;
     P.tape = (flips && multiplicities) ? 1 : 0;
     P.prod = 0;
+    P.chain_base = static_cast<uint32_t>(cfg->chain_base > 0 ? cfg->chain_base : 0);
     if (steps > 0)
         SCU(launch_sampler(PNS_DENSE, qt, 4, T, P, static_cast<int>(ctas), per_cta * 32 * T,
                            static_cast<size_t>(per_cta) * chain_bytes, s));

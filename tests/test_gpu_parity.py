@@ -192,3 +192,16 @@ def test_invalid_inputs_rejected(bad):
     with pytest.raises(expect) as ei:
         pns.Sampler([prob], **kw)
     assert ei.value.status == status
+
+
+def test_sharded_contexts_equal_one_context():
+    """Instances split over two contexts (as over two GPUs) with chain_base /
+    group_base give the records of the single context."""
+    probs = [_int_problem(64, seed=3, dtype=np.int32, betas=(0.1, 0.2)),
+             _int_problem(96, seed=4, dtype=np.int32, betas=(0.3, 0.4))]
+    cfg = dict(variant="unbiased", k=8, chains_per_replica=3, seed=5)
+    whole = gpu_run(probs, 600, tape=True, **cfg)
+    a = gpu_run(probs[:1], 600, tape=True, **cfg)
+    b = gpu_run(probs[1:], 600, tape=True, chain_base=6, group_base=3, **cfg)
+    np.testing.assert_array_equal(np.concatenate([a["flips"], b["flips"]]), whole["flips"])
+    np.testing.assert_array_equal(np.concatenate([a["m"], b["m"]]), whole["m"])

@@ -68,6 +68,7 @@ struct pns_ctx {
     int R = 1;  // exchange group size
     // device memory
     void *d_q = nullptr;
+    size_t q_bytes = 0;
     int32_t *d_rowptr = nullptr, *d_col = nullptr;
     void *d_diag = nullptr, *d_b = nullptr;
     float *d_betas = nullptr;
@@ -339,6 +340,7 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     // ---- upload ---------------------------------------------------------------
     const size_t q_bytes = static_cast<size_t>(std::max<int64_t>(q_elems, 1)) * (c->fmt == PNS_DENSE ? qb : vb);
     CU(cudaMalloc(&c->d_q, q_bytes));
+    c->q_bytes = q_bytes;
     CU(cudaMemsetAsync(c->d_q, 0, q_bytes, s));
     CU(cudaMalloc(&c->d_diag, static_cast<size_t>(vec_elems) * vb));
     CU(cudaMalloc(&c->d_b, static_cast<size_t>(vec_elems) * vb));
@@ -644,6 +646,9 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.pt = pt ? 1 : 0;
     P.tape = c->cfg.tape;
     P.prod = c->prod;
+    // speculative row loads for Unbiased PNS when Q does not stay in L2
+    P.prefetch = (c->cfg.variant == PNS_UNBIASED && c->q_bytes > (64ull << 20)) ? 1 : 0;
+    if (const char *e = getenv("PNS_PREFETCH")) P.prefetch = atoi(e) ? 1 : 0;
     P.chain_base = static_cast<uint32_t>(c->cfg.chain_base);
     P.group_base = static_cast<uint32_t>(c->cfg.group_base);
     auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {

@@ -86,6 +86,8 @@ struct KParams {
     int32_t prod;           // producer warps per chain (0: consumers draw their own numbers)
     uint32_t chain_base;    // global id of chain 0 (Philox stream id = chain_base + chain)
     uint32_t group_base;    // global id of exchange group 0
+    int32_t prefetch;       // Unbiased: start the winner's row load before the budget test
+    int32_t pad2;
 };
 
 PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }

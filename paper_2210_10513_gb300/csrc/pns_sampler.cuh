@@ -244,7 +244,7 @@ __device__ __forceinline__ bool draw_subset_warp(uint64_t seed, uint32_t chain, 
 }
 
 constexpr int CPT = 4;  // candidates per consumer thread kept in registers
-constexpr int PF = 4;   // row chunks per consumer thread loaded ahead of the move
+constexpr int PF = 8;   // row chunks per consumer thread loaded ahead of the move
 
 // ---------------------------------------------------------------------------
 // The kernel.  TC consumer warps per chain; P.prod producer warps (0 or 1).
@@ -440,18 +440,19 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                 const int c = ctid + u * TCC;
                 if (c < chunks) add_chunk<QT, HT>(h + c * VE, pre[u], up);
             }
-            int c = ctid + PF * TCC;
-            for (; c + 3 * TCC < chunks; c += 4 * TCC) {
-                const uint4 v0 = ld_nc_v4(row + (c + 0 * TCC) * VE);
-                const uint4 v1 = ld_nc_v4(row + (c + 1 * TCC) * VE);
-                const uint4 v2 = ld_nc_v4(row + (c + 2 * TCC) * VE);
-                const uint4 v3 = ld_nc_v4(row + (c + 3 * TCC) * VE);
-                add_chunk<QT, HT>(h + (c + 0 * TCC) * VE, v0, up);
-                add_chunk<QT, HT>(h + (c + 1 * TCC) * VE, v1, up);
-                add_chunk<QT, HT>(h + (c + 2 * TCC) * VE, v2, up);
-                add_chunk<QT, HT>(h + (c + 3 * TCC) * VE, v3, up);
+            // the rest in batches of PF loads in flight per thread
+            for (int c0 = ctid + PF * TCC; c0 < chunks; c0 += PF * TCC) {
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    const int c = c0 + u * TCC;
+                    if (c < chunks) pre[u] = ld_nc_v4(row + c * VE);
+                }
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    const int c = c0 + u * TCC;
+                    if (c < chunks) add_chunk<QT, HT>(h + c * VE, pre[u], up);
+                }
             }
-            for (; c < chunks; c += TCC) add_chunk<QT, HT>(h + c * VE, ld_nc_v4(row + c * VE), up);
         }
         sync_cons();  // every consumer has read x_j
         if (ctid == 0) xw[j >> 5] ^= 1u << (j & 31);
@@ -647,8 +648,10 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                 S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
             }
             const int j = cand(static_cast<int>(wpos), sl);
-            // Basic and RF always move: start the row load before the multiplicity
-            const bool always_move = variant != VAR_UNBIASED;
+            // Basic and RF always move: start the row load before the multiplicity.
+            // For Unbiased PNS the load is speculative when P.prefetch is set
+            // (rows from HBM, where the latency matters more than the bytes).
+            const bool always_move = variant != VAR_UNBIASED || P.prefetch;
             if (always_move) prefetch_row(j);
             // a5: multiplicity and budget
             const Mult mu = multiplicity_e1(S, k, anchor_f, rd.e1);

@@ -21,8 +21,9 @@ def _problems(ns, seed=0, integer=False):
     return probs
 
 
-@pytest.mark.parametrize("integer", [False, True])
-def test_unbiased_tempering_matches_oracle(integer):
+@pytest.mark.parametrize("integer,prefetch", [(False, "0"), (True, "0"), (False, "1")])
+def test_unbiased_tempering_matches_oracle(monkeypatch, integer, prefetch):
+    monkeypatch.setenv("PNS_PREFETCH", prefetch)
     ns = [130, 257, 96]
     betas = synth.geometric_ladder(0.1, 10.0, 4)
     probs = _problems(ns, seed=3, integer=integer)

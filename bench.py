@@ -194,7 +194,8 @@ def gpu_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)  # non-default stream: pns_run replays a captured CUDA graph
+    torch.cuda.set_stream(stream)
     seed = args.seed + rank  # weak scaling: each rank samples its own independent chains
     q, b = workload(args.seed)
     qd = torch.from_numpy(q).to(dev)
@@ -202,8 +203,10 @@ def gpu_arm(args):
     records = args.records
 
     def make(variant, **kw):
+        opts = dict(graph=True, autotune=not args.no_autotune)
+        opts.update(kw)
         return pns.Sampler([dict(n=N, q=qd, b=bd, betas=[BETA])], variant=variant, k=K, chains_per_replica=CHAINS,
-                           L0=L0, seed=seed, tape=False, **kw)
+                           L0=L0, seed=seed, tape=False, **opts)
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -258,7 +261,7 @@ def gpu_arm(args):
         extra["basic_samples_per_s"] = d_b["steps"] / (sum(ms_b) / 1e3)
         s_basic.close()
         # plain form: one chain per launch, launches back to back
-        s_plain = make("unbiased", chains_per_cta=1)
+        s_plain = make("unbiased", chains_per_cta=1, graph=False, autotune=False)
         plain_records = max(100, records // 10)
         ms_p, d_p = timed(s_plain, 1, 1, plain=True, recs=plain_records)
         extra["plain_samples_per_s"] = d_p["steps"] / (sum(ms_p) / 1e3)
@@ -333,7 +336,10 @@ def gpu_arm(args):
                      "algorithmic_bytes": "2048 B (one int16 row of Q) per flip"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
         "clocks": clk.summary(), "wall_s": wall,
-        "mapping": {"warps_per_chain": info.warps_per_chain, "ctas": info.ctas},
+        "mapping": {"warps_per_chain": info.warps_per_chain, "team_warps": info.team_warps,
+                    "producer_warps": info.producer_warps, "spec_depth": info.spec_depth, "ctas": info.ctas,
+                    "autotune": not args.no_autotune,
+                    "cuda_graph": True},
     }
     line.update(extra)
     print(json.dumps(line), flush=True)
@@ -411,7 +417,9 @@ def side_workload(args):
     from paper_2210_10513_gb300 import pns
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    tune = dict(graph=True, autotune=not args.no_autotune)
     if args.workload == "tempering":
         n_inst = args.instances
         probs, ladder = synth.workload_tempering(n_inst, seed=args.seed)
@@ -419,7 +427,7 @@ def side_workload(args):
         for pr in probs:
             plist.append(dict(n=pr["n"], q=torch.from_numpy(pr["q"]).to(dev), betas=ladder, k=max(1, pr["n"] // 16)))
         s = pns.Sampler(plist, variant="unbiased", k=1, chains_per_replica=1, L0=100, swap_interval=100,
-                        seed=args.seed, tape=False)
+                        seed=args.seed, tape=False, **tune)
         per_step = 1000
         ns = np.repeat(np.array([pr["n"] for pr in probs]), len(ladder))
         row_bytes = 4 * ns
@@ -432,7 +440,7 @@ def side_workload(args):
         csr = synth.lattice_csr(side, seed=args.seed)
         csr_d = tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in csr)
         s = pns.Sampler([dict(n=side * side, csr=csr_d, betas=[0.2, 0.44, 1.0])], variant="unbiased", k=1024,
-                        chains_per_replica=64, L0=100, seed=args.seed, tape=False)
+                        chains_per_replica=64, L0=100, seed=args.seed, tape=False, **tune)
         per_step = args.records
         row_bytes = np.full(s.info.chains, 5 * 4 + 4, dtype=np.int64)
         desc = ("lattice: 256x256 periodic +-1 couplings, CSR, 64 chains x beta {0.2,0.44,1.0}, Unbiased k=1024, "
@@ -468,6 +476,8 @@ def side_workload(args):
             "ms_per_step": secs * 1e3 / args.steps, "steps": args.steps, "warmup": args.warmup,
             "row_bytes_per_s_GBs": byts / secs / 1e9, "hbm_peak_GBs": hbm, "frac_of_hbm": byts / secs / 1e9 / hbm,
             "chains": int(s.info.chains), "ctas": int(s.info.ctas), "warps_per_chain": int(s.info.warps_per_chain),
+            "mapping": {"team_warps": s.info.team_warps, "producer_warps": s.info.producer_warps,
+                        "spec_depth": s.info.spec_depth, "autotune": not args.no_autotune, "cuda_graph": True},
             "swaps_accepted": int((after["swaps_accepted"] - before["swaps_accepted"]).sum()),
             "config": {"workload": desc}, "clocks": clk.summary()}
     s.close()
@@ -483,6 +493,7 @@ def main():
     ap.add_argument("--records", type=int, default=10000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="heuristic chain-to-CTA mapping")
     ap.add_argument("--quick", action="store_true", help="skip the Basic / plain side measurements")
     ap.add_argument("--workload", default="dense1024", choices=["dense1024", "tempering", "lattice", "fit"])
     ap.add_argument("--instances", type=int, default=512)

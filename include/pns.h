@@ -108,6 +108,16 @@ typedef struct {
     const uint32_t *x0;        /* NULL (all zeros) or initial bit-packed states: chain c,
                                   bit i at word c*W + i/32, bit i%32; W = pns_info.words_per_chain */
     int32_t group_base;        /* global id of this context's first exchange group, >= 0 */
+    int32_t graph;             /* 1: pns_run captures its launch into a CUDA graph once per step
+                                  count (and stream) and replays it; records are identical to
+                                  direct launches.  On the legacy default stream (NULL) the
+                                  kernel is launched directly.  The first call for a new step
+                                  count captures: make it outside any capture of your own. */
+    int32_t autotune;          /* 1: pns_create times the candidate chain-to-CTA mappings
+                                  (warps per chain, producer warps, speculation depth, chains
+                                  per CTA) on short probe runs and keeps the fastest; results
+                                  do not depend on the mapping.  Choices are cached in the file
+                                  named by PNS_AUTOTUNE_CACHE when that variable is set. */
     int32_t reserved;          /* must be 0 */
 } pns_config;
 
@@ -121,8 +131,12 @@ typedef struct {
     int32_t field_bytes;       /* bytes per field element (1, 2, 4) */
     int32_t field_is_float;    /* 1: fp32 fields, 0: signed integers */
     int64_t tape_capacity;     /* records per chain held by the tape of the last pns_run */
-    int32_t warps_per_chain;   /* mapping in use */
+    int32_t warps_per_chain;   /* mapping in use: warps that serve one chain (all kinds) */
     int32_t ctas;              /* CTAs of the sampling launch */
+    int32_t team_warps;        /* warps evaluating the chain's candidates (non-speculative kernel) */
+    int32_t producer_warps;    /* warps precomputing the next record's random numbers */
+    int32_t spec_depth;        /* speculative kernel: records evaluated at once (0: not used) */
+    int32_t reserved;
 } pns_info;
 
 typedef struct {

@@ -90,12 +90,21 @@ struct pns_ctx {
     int n_cta = 0, block = 32;
     size_t smem = 0;
     int latched = 0;
+    std::vector<ChainDesc> h_chains;  // host copy of the chain descriptors (smem offsets per mapping)
+    int num_sms = 0, smem_optin = 0;
+    int per_cta = 0;
+    // CUDA graph of the last pns_run launch
+    cudaGraphExec_t gexec = nullptr;
+    int64_t g_steps = -1;
+    cudaStream_t g_stream = nullptr;
+    bool tape_off = false;  // autotuner probes run without the tape
 };
 
 namespace {
 
 void free_ctx(pns_ctx *c) {
     if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void *ptrs[] = {c->d_q, c->d_rowptr, c->d_col, c->d_diag, c->d_b, c->d_betas, c->d_inst, c->d_chain,
                     c->d_state, c->d_x, c->d_fields, c->d_cta, c->d_cta_chains, c->d_status, c->d_tape_flip,
                     c->d_tape_m,  c->d_tape_x, c->d_tape_E};
@@ -118,6 +127,8 @@ pns_status check_args(const pns_problem *probs, int32_t n_probs, const pns_confi
     if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32))
         return fail(PNS_ERR_INVALID_ARG, "warps_per_chain must be 0, 1, 2, 4, 8, 16 or 32");
     if (cfg->swap_interval < 0) return fail(PNS_ERR_INVALID_ARG, "swap_interval must be >= 0");
+    if (cfg->graph != 0 && cfg->graph != 1) return fail(PNS_ERR_INVALID_ARG, "graph must be 0 or 1");
+    if (cfg->autotune != 0 && cfg->autotune != 1) return fail(PNS_ERR_INVALID_ARG, "autotune must be 0 or 1");
     if (cfg->chains_per_cta < 0 || cfg->reserved != 0 || cfg->chain_base < 0 || cfg->group_base < 0)
         return fail(PNS_ERR_INVALID_ARG, "chains_per_cta, chain_base, group_base must be >= 0 and reserved 0");
     if (cfg->swap_interval > 0) {
@@ -265,6 +276,239 @@ static int auto_warps(const pns_ctx &c) {
     return T;
 }
 
+// A chain-to-CTA mapping: warps per chain, producer warps, speculation depth.
+struct Mapping {
+    int T = 1, prod = 0, spec = 0, per_cta = 0;
+};
+
+static bool spec_allowed(const pns_ctx &c) {
+    int kmax = 1;
+    for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
+    return c.fmt == PNS_DENSE && c.cfg.swap_interval == 0 && c.cfg.L0 < (1ll << 31) && kmax <= 128 &&
+           (c.cfg.variant == PNS_UNBIASED || c.cfg.variant == PNS_METROPOLIS);
+}
+
+// The heuristic mapping (and the environment overrides used by the tests).
+static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
+    const pns_config *cfg = &c.cfg;
+    m.per_cta = c.per_cta;
+    m.T = cfg->warps_per_chain > 0 ? cfg->warps_per_chain : auto_warps(c);
+    if (!sampler_supported(c.fmt, c.qtype, c.hbytes, m.T)) {
+        if (cfg->warps_per_chain > 0)
+            return fail(PNS_ERR_UNSUPPORTED, "warps_per_chain = %d is not built for this format", m.T);
+        m.T = 1;
+    }
+    // A producer warp per chain pays off when the GPU is latency-bound (few
+    // warps per SM); with many chains every warp already has work.
+    // Producer warps: one per 32 race numbers, plus one for the record scalars.
+    int kmax = 1;
+    for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
+    const int prod_want = cfg->variant == PNS_METROPOLIS ? 1 : std::min(3, 1 + (kmax + 31) / 32);
+    m.prod = 0;
+    if (m.T < 32 && c.chains * m.T <= 8ll * c.num_sms) m.prod = prod_want;
+    if (const char *e = getenv("PNS_PRODUCER_WARPS")) m.prod = std::max(0, std::min(3, atoi(e)));
+    if (m.T + m.prod > 16 || (m.T == 32 && m.prod > 0)) m.prod = 0;
+    // Speculative evaluation (Unbiased / Metropolis, dense, no exchange): a
+    // stay leaves the state unchanged, so D warps evaluate D future records at
+    // once.  Used when the GPU would otherwise be latency-bound.
+    m.spec = 0;
+    if (spec_allowed(c) && cfg->warps_per_chain == 0) {
+        if (c.chains * 8 <= 16ll * c.num_sms) m.spec = 8;
+        else if (c.chains * 4 <= 16ll * c.num_sms) m.spec = 4;
+    }
+    if (const char *e = getenv("PNS_SPEC_DEPTH")) {
+        const int d = atoi(e);
+        m.spec = (d == 0 || spec_supported(c.qtype, d)) ? d : 0;
+    }
+    if (m.spec > 0 && !spec_allowed(c)) m.spec = 0;
+    if (m.spec > 0) m.prod = 0;
+    return PNS_OK;
+}
+
+// Plans the CTAs for a mapping and installs the descriptors on the device
+// (fewer producer warps when an exchange group or the barrier budget does not
+// fit with them).
+static pns_status apply_mapping(pns_ctx *c, Mapping m, cudaStream_t s) {
+    pns_status st;
+    PlanOut pl;
+    while (true) {
+        c->T = m.T;
+        c->prod = m.prod;
+        c->spec = m.spec;
+        pl = PlanOut();
+        st = plan(*c, c->h_chains, c->num_sms, static_cast<size_t>(c->smem_optin), m.per_cta, pl);
+        if (st == PNS_OK || m.prod == 0) break;
+        m.prod -= 1;
+    }
+    if (st != PNS_OK) return st;
+    std::vector<ChainDesc> chains = c->h_chains;
+    for (int64_t i = 0; i < c->chains; ++i) chains[i].smem_off = pl.smem_off[i];
+    if (c->d_chain) cudaFree(c->d_chain);
+    if (c->d_cta) cudaFree(c->d_cta);
+    if (c->d_cta_chains) cudaFree(c->d_cta_chains);
+    c->d_chain = nullptr;
+    c->d_cta = nullptr;
+    c->d_cta_chains = nullptr;
+    c->n_cta = static_cast<int>(pl.cta.size());
+    c->block = pl.block;
+    c->smem = pl.smem;
+    CU(cudaMalloc(&c->d_chain, sizeof(ChainDesc) * chains.size()));
+    CU(cudaMemcpyAsync(c->d_chain, chains.data(), sizeof(ChainDesc) * chains.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMalloc(&c->d_cta, sizeof(CtaDesc) * pl.cta.size()));
+    CU(cudaMemcpyAsync(c->d_cta, pl.cta.data(), sizeof(CtaDesc) * pl.cta.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMalloc(&c->d_cta_chains, sizeof(int32_t) * pl.cta_chains.size()));
+    CU(cudaMemcpyAsync(c->d_cta_chains, pl.cta_chains.data(), sizeof(int32_t) * pl.cta_chains.size(),
+                       cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        c->g_steps = -1;
+    }
+    return PNS_OK;
+}
+
+static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain);
+
+// Key of a problem shape for the autotuner cache.
+static std::string tune_key(const pns_ctx &c) {
+    int64_t n_sum = 0, n_max = 0, k_max = 0;
+    for (const InstHost &ih : c.inst) {
+        n_sum += ih.n;
+        n_max = std::max<int64_t>(n_max, ih.n);
+        k_max = std::max<int64_t>(k_max, ih.k);
+    }
+    char buf[256];
+    snprintf(buf, sizeof(buf), "v%d f%d q%d h%d sub%d pt%lld inst%zu nsum%lld nmax%lld kmax%lld chains%lld sms%d",
+             c.cfg.variant, c.fmt, c.qtype, c.hbytes, c.cfg.subset, (long long)c.cfg.swap_interval, c.inst.size(),
+             (long long)n_sum, (long long)n_max, (long long)k_max, (long long)c.chains, c.num_sms);
+    return buf;
+}
+
+// Times candidate mappings on short probe runs from a snapshot of the chain
+// state (restored after each probe, so the chains are untouched) and keeps
+// the fastest.  The records a chain produces do not depend on the mapping.
+static pns_status autotune(pns_ctx *c, cudaStream_t s) {
+    const std::string key = tune_key(*c);
+    const char *path = getenv("PNS_AUTOTUNE_CACHE");
+    if (path) {
+        if (FILE *f = fopen(path, "r")) {
+            char line[512];
+            while (fgets(line, sizeof(line), f)) {
+                const char *bar = strchr(line, '|');
+                if (!bar) continue;
+                if (std::string(line, bar - line) == key) {
+                    Mapping m;
+                    if (sscanf(bar + 1, "%d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta) == 4) {
+                        fclose(f);
+                        return apply_mapping(c, m, s);
+                    }
+                }
+            }
+            fclose(f);
+        }
+    }
+    std::vector<Mapping> cands;
+    Mapping base;
+    pns_status st = default_mapping(*c, base);
+    if (st != PNS_OK) return st;
+    cands.push_back(base);
+    const int Ts_dense[] = {1, 2, 4};
+    const int Ts_csr[] = {1, 4, 8, 16, 32};
+    const int T_fixed = c->cfg.warps_per_chain;  // an explicit choice is kept
+    auto add = [&](Mapping m) {
+        if (T_fixed > 0 && (m.T != T_fixed || m.spec > 0)) return;
+        if (!sampler_supported(c->fmt, c->qtype, c->hbytes, m.T)) return;
+        if (m.spec > 0 && (!spec_allowed(*c) || !spec_supported(c->qtype, m.spec))) return;
+        for (const Mapping &o : cands)
+            if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta) return;
+        cands.push_back(m);
+    };
+    if (c->fmt == PNS_DENSE) {
+        for (int T : Ts_dense)
+            for (int prod = 0; prod <= 3; ++prod) add(Mapping{T, prod, 0, c->per_cta});
+        add(Mapping{8, 0, 0, c->per_cta});
+        for (int d : {4, 8, 16}) add(Mapping{1, 0, d, c->per_cta});
+    } else {
+        for (int T : Ts_csr) add(Mapping{T, 0, 0, c->per_cta});
+    }
+    // Snapshots: the chains as created (restored at the end) and after a
+    // burn-in with the heuristic mapping, from which every candidate is timed
+    // (a chain started from its initial state moves far more often than in
+    // equilibrium, which would favour the wrong mapping).
+    const size_t b_state = sizeof(ChainState) * c->chains, b_x = sizeof(uint32_t) * c->W * c->chains,
+                 b_f = static_cast<size_t>(c->hbytes) * c->LD * c->chains, b_all = b_state + b_x + b_f;
+    void *snap = nullptr;
+    CU(cudaMalloc(&snap, 2 * b_all));
+    struct FreeSnap {
+        void *p;
+        ~FreeSnap() { cudaFree(p); }
+    } fs{snap};
+    char *orig = static_cast<char *>(snap), *burned = orig + b_all;
+    auto save = [&](char *dst) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dst, c->d_state, b_state, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + b_state, c->d_x, b_x, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + b_state + b_x, c->d_fields, b_f, cudaMemcpyDeviceToDevice, s);
+        return e;
+    };
+    auto load = [&](const char *src) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(c->d_state, src, b_state, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_x, src + b_state, b_x, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_fields, src + b_state + b_x, b_f, cudaMemcpyDeviceToDevice, s);
+        return e;
+    };
+    int64_t n_max = 1;
+    for (const InstHost &ih : c->inst) n_max = std::max<int64_t>(n_max, ih.n);
+    const int64_t swap = c->cfg.swap_interval;
+    auto round_up = [&](int64_t v) { return swap > 0 ? (v + swap - 1) / swap * swap : v; };
+    const int64_t burn = round_up(std::min<int64_t>(16 * n_max, 65536));
+    const int64_t warm = round_up(64), probe = round_up(1024);
+    CU(save(orig));
+    c->tape_off = true;
+    struct TapeOn {
+        pns_ctx *c;
+        ~TapeOn() { c->tape_off = false; }
+    } tape_on{c};
+    pns_status st_b = run_impl(c, burn, s, false);
+    if (st_b != PNS_OK) return st_b;
+    CU(save(burned));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    Mapping best = base;
+    for (const Mapping &m : cands) {
+        if (apply_mapping(c, m, s) != PNS_OK) continue;
+        if (run_impl(c, warm, s, false) != PNS_OK) continue;  // first launch of this kernel
+        CU(load(burned));
+        CU(cudaEventRecord(e0, s));
+        pns_status rs = run_impl(c, probe, s, false);
+        CU(cudaEventRecord(e1, s));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (rs == PNS_OK && ms < best_ms) {
+            best_ms = ms;
+            best = m;
+        }
+        CU(load(burned));
+    }
+    CU(load(orig));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CU(cudaStreamSynchronize(s));
+    int32_t code = 0;
+    CU(cudaMemcpy(&code, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (code != 0) return fail(static_cast<pns_status>(code), "device error while autotuning");
+    if (path) {
+        if (FILE *f = fopen(path, "a")) {
+            fprintf(f, "%s|%d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta);
+            fclose(f);
+        }
+    }
+    return apply_mapping(c, best, s);
+}
+
 extern "C" {
 
 const char *pns_last_error(void) { return g_err.c_str(); }
@@ -281,6 +525,10 @@ pns_status pns_get_info(const pns_ctx *ctx, pns_info *info) {
     info->tape_capacity = ctx->tape_cap;
     info->warps_per_chain = ctx->spec > 0 ? ctx->spec : ctx->T + ctx->prod;
     info->ctas = ctx->n_cta;
+    info->team_warps = ctx->spec > 0 ? 0 : ctx->T;
+    info->producer_warps = ctx->spec > 0 ? 0 : ctx->prod;
+    info->spec_depth = ctx->spec;
+    info->reserved = 0;
     return PNS_OK;
 }
 
@@ -484,67 +732,17 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     if (c->chains > (1ll << 31) - 1) return fail(PNS_ERR_INVALID_ARG, "too many chains");
 
     // ---- mapping ------------------------------------------------------------------
-    c->T = cfg->warps_per_chain > 0 ? cfg->warps_per_chain : auto_warps(*c);
-    if (!sampler_supported(c->fmt, c->qtype, c->hbytes, c->T)) {
-        if (cfg->warps_per_chain > 0)
-            return fail(PNS_ERR_UNSUPPORTED, "warps_per_chain = %d is not built for this format", c->T);
-        c->T = 1;
-    }
-    // A producer warp per chain pays off when the GPU is latency-bound (few
-    // warps per SM); with many chains every warp already has work.
-    // Producer warps: one per 32 race numbers, plus one for the record scalars.
-    int kmax = 1;
-    for (const InstHost &ih : c->inst) kmax = std::max(kmax, ih.k);
-    const int prod_want = cfg->variant == PNS_METROPOLIS ? 1 : std::min(3, 1 + (kmax + 31) / 32);
-    c->prod = 0;
-    if (c->T < 32) {
-        const int64_t warps = c->chains * c->T;
-        c->prod = warps <= 8ll * num_sms ? prod_want : 0;
-    }
-    if (const char *e = getenv("PNS_PRODUCER_WARPS")) c->prod = std::max(0, std::min(3, atoi(e)));
-    if (c->T + c->prod > 16 || (c->T == 32 && c->prod > 0)) c->prod = 0;
-    PlanOut pl;
-    int per_cta = cfg->chains_per_cta;
-    if (per_cta == 0)
-        if (const char *e = getenv("PNS_CHAINS_PER_CTA")) per_cta = atoi(e);
-    // Speculative evaluation (Unbiased / Metropolis, dense, no exchange): a
-    // stay leaves the state unchanged, so D warps evaluate D future records at
-    // once.  Used when the GPU would otherwise be latency-bound.
-    c->spec = 0;
-    if (c->fmt == PNS_DENSE && cfg->swap_interval == 0 && cfg->L0 < (1ll << 31) &&
-        (cfg->variant == PNS_UNBIASED || cfg->variant == PNS_METROPOLIS) && kmax <= 128 &&
-        cfg->warps_per_chain == 0) {
-        if (c->chains * 8 <= 16ll * num_sms) c->spec = 8;
-        else if (c->chains * 4 <= 16ll * num_sms) c->spec = 4;
-    }
-    if (const char *e = getenv("PNS_SPEC_DEPTH")) {
-        const int d = atoi(e);
-        c->spec = (d == 0 || spec_supported(c->qtype, d)) ? d : 0;
-    }
-    if (c->spec > 0 && !(c->fmt == PNS_DENSE && cfg->swap_interval == 0 && cfg->L0 < (1ll << 31) &&
-                         (cfg->variant == PNS_UNBIASED || cfg->variant == PNS_METROPOLIS)))
-        c->spec = 0;
-    if (c->spec > 0) c->prod = 0;
-    // fewer producer warps when an exchange group or the barrier budget does
-    // not fit with them
-    while (true) {
-        pl = PlanOut();
-        st = plan(*c, chains, num_sms, static_cast<size_t>(smem_optin), per_cta, pl);
-        if (st == PNS_OK || c->prod == 0) break;
-        c->prod -= 1;
-    }
+    c->h_chains = chains;
+    c->num_sms = num_sms;
+    c->smem_optin = smem_optin;
+    c->per_cta = cfg->chains_per_cta;
+    if (c->per_cta == 0)
+        if (const char *e = getenv("PNS_CHAINS_PER_CTA")) c->per_cta = atoi(e);
+    Mapping mp;
+    st = default_mapping(*c, mp);
     if (st != PNS_OK) return st;
-    for (int64_t i = 0; i < c->chains; ++i) chains[i].smem_off = pl.smem_off[i];
-    c->n_cta = static_cast<int>(pl.cta.size());
-    c->block = pl.block;
-    c->smem = pl.smem;
-    CU(cudaMalloc(&c->d_chain, sizeof(ChainDesc) * chains.size()));
-    CU(cudaMemcpyAsync(c->d_chain, chains.data(), sizeof(ChainDesc) * chains.size(), cudaMemcpyHostToDevice, s));
-    CU(cudaMalloc(&c->d_cta, sizeof(CtaDesc) * pl.cta.size()));
-    CU(cudaMemcpyAsync(c->d_cta, pl.cta.data(), sizeof(CtaDesc) * pl.cta.size(), cudaMemcpyHostToDevice, s));
-    CU(cudaMalloc(&c->d_cta_chains, sizeof(int32_t) * pl.cta_chains.size()));
-    CU(cudaMemcpyAsync(c->d_cta_chains, pl.cta_chains.data(), sizeof(int32_t) * pl.cta_chains.size(),
-                       cudaMemcpyHostToDevice, s));
+    st = apply_mapping(c, mp, s);
+    if (st != PNS_OK) return st;
 
     // ---- chain state ------------------------------------------------------------------
     CU(cudaMalloc(&c->d_state, sizeof(ChainState) * c->chains));
@@ -578,10 +776,16 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     CU(launch_init_fields(c->fmt, c->qtype, c->hbytes, c->d_inst, c->d_chain, c->d_x, c->d_fields, c->d_state,
                           c->chains, c->W, c->LD, c->max_ld, s));
     CU(cudaStreamSynchronize(s));
+    if (cfg->autotune) {
+        st = autotune(c, s);
+        if (st != PNS_OK) return st;
+    }
     guard.keep = true;
     *out = c;
     return PNS_OK;
 }
+
+}  // extern "C"
 
 static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) {
     if (!c) return fail(PNS_ERR_INVALID_ARG, "ctx is NULL");
@@ -596,7 +800,7 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
         if (c->cfg.variant == PNS_UNBIASED) cap = steps / c->cfg.L0 * (c->cfg.L0 + 1);
     }
     if (steps == 0) return PNS_OK;
-    if (c->cfg.tape) {
+    if (c->cfg.tape && !c->tape_off) {
         if (cap > c->tape_alloc) {
             if (c->d_tape_flip) cudaFree(c->d_tape_flip);
             if (c->d_tape_m) cudaFree(c->d_tape_m);
@@ -614,6 +818,10 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
                 CU(cudaMalloc(&c->d_tape_E, sizeof(double) * cap * c->chains));
             }
             c->tape_alloc = cap;
+            if (c->gexec) {
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
         }
         c->tape_cap = cap;
     } else {
@@ -644,7 +852,7 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.LD = c->LD;
     P.R = pt ? c->R : 1;
     P.pt = pt ? 1 : 0;
-    P.tape = c->cfg.tape;
+    P.tape = c->tape_off ? 0 : c->cfg.tape;
     P.prod = c->prod;
     // speculative row loads for Unbiased PNS when Q does not stay in L2
     P.prefetch = (c->cfg.variant == PNS_UNBIASED && c->q_bytes > (64ull << 20)) ? 1 : 0;
@@ -655,7 +863,32 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
         if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->block, c->smem, s);
         return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->block, c->smem, s);
     };
-    if (!plain) {
+    if (!plain && c->cfg.graph && s != nullptr && !c->tape_off) {
+        // one captured launch per step count; the chain state lives in device
+        // memory, so replaying the same graph continues the chains
+        if (!c->gexec || c->g_steps != steps || c->g_stream != s) {
+            if (c->gexec) {
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+            const cudaError_t le = launch(P, c->n_cta);
+            const cudaError_t ce = cudaStreamEndCapture(s, &g);
+            if (g && (le != cudaSuccess || ce != cudaSuccess)) cudaGraphDestroy(g);
+            if (le != cudaSuccess) return fail(PNS_ERR_CUDA, "capture: %s", cudaGetErrorString(le));
+            if (ce != cudaSuccess) return fail(PNS_ERR_CUDA, "capture: %s", cudaGetErrorString(ce));
+            const cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                c->gexec = nullptr;
+                return fail(PNS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+            }
+            c->g_steps = steps;
+            c->g_stream = s;
+        }
+        CU(cudaGraphLaunch(c->gexec, s));
+    } else if (!plain) {
         CU(launch(P, c->n_cta));
     } else {
         for (int b = 0; b < c->n_cta; ++b) {
@@ -665,6 +898,8 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     }
     return PNS_OK;
 }
+
+extern "C" {
 
 pns_status pns_run(pns_ctx *c, int64_t steps, void *stream) { return run_impl(c, steps, stream, false); }
 

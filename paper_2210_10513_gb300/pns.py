@@ -41,13 +41,15 @@ class pns_config(C.Structure):
     _fields_ = [("variant", C.c_int32), ("k", C.c_int32), ("subset", C.c_int32), ("chains_per_replica", C.c_int32),
                 ("L0", C.c_int64), ("swap_interval", C.c_int64), ("seed", C.c_uint64), ("tape", C.c_int32),
                 ("warps_per_chain", C.c_int32), ("chains_per_cta", C.c_int32), ("chain_base", C.c_int32),
-                ("x0", C.c_void_p), ("group_base", C.c_int32), ("reserved", C.c_int32)]
+                ("x0", C.c_void_p), ("group_base", C.c_int32), ("graph", C.c_int32), ("autotune", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class pns_info(C.Structure):
     _fields_ = [("chains", C.c_int64), ("words_per_chain", C.c_int32), ("field_stride", C.c_int32),
                 ("field_bytes", C.c_int32), ("field_is_float", C.c_int32), ("tape_capacity", C.c_int64),
-                ("warps_per_chain", C.c_int32), ("ctas", C.c_int32)]
+                ("warps_per_chain", C.c_int32), ("ctas", C.c_int32), ("team_warps", C.c_int32),
+                ("producer_warps", C.c_int32), ("spec_depth", C.c_int32), ("reserved", C.c_int32)]
 
 
 class pns_moment_scalars(C.Structure):
@@ -194,7 +196,8 @@ def make_problem(n, q=None, b=None, betas=(1.0,), csr=None, k=0, keep=None):
 
 
 def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100, swap_interval=0, seed=0,
-                tape=False, warps_per_chain=0, x0=None, chains_per_cta=0, chain_base=0, group_base=0):
+                tape=False, warps_per_chain=0, x0=None, chains_per_cta=0, chain_base=0, group_base=0, graph=False,
+                autotune=False):
     c = pns_config()
     c.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     c.k = int(k)
@@ -208,6 +211,8 @@ def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica
     c.chains_per_cta = int(chains_per_cta)
     c.chain_base = int(chain_base)
     c.group_base = int(group_base)
+    c.graph = int(bool(graph))
+    c.autotune = int(bool(autotune))
     c.x0 = _addr(x0)
     return c
 
@@ -290,7 +295,7 @@ class Sampler:
 
     def __init__(self, problems, variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100,
                  swap_interval=0, seed=0, tape=False, warps_per_chain=0, x0=None, stream=None, chains_per_cta=0,
-                 chain_base=0, group_base=0):
+                 chain_base=0, group_base=0, graph=False, autotune=False):
         keep = []
         probs = []
         for pr in problems:
@@ -298,7 +303,7 @@ class Sampler:
         if x0 is not None:
             keep.append(x0)
         cfg = make_config(variant, k, subset, chains_per_replica, L0, swap_interval, seed, tape, warps_per_chain, x0,
-                          chains_per_cta, chain_base, group_base)
+                          chains_per_cta, chain_base, group_base, graph, autotune)
         self.ctx = pns_create(probs, cfg, stream)
         self.info = pns_get_info(self.ctx)
         self.tape = bool(tape)

@@ -477,7 +477,8 @@ def side_workload(args):
             "row_bytes_per_s_GBs": byts / secs / 1e9, "hbm_peak_GBs": hbm, "frac_of_hbm": byts / secs / 1e9 / hbm,
             "chains": int(s.info.chains), "ctas": int(s.info.ctas), "warps_per_chain": int(s.info.warps_per_chain),
             "mapping": {"team_warps": s.info.team_warps, "producer_warps": s.info.producer_warps,
-                        "spec_depth": s.info.spec_depth, "autotune": not args.no_autotune, "cuda_graph": True},
+                        "spec_depth": s.info.spec_depth, "period_blocked": s.info.period_blocked,
+                        "autotune": not args.no_autotune, "cuda_graph": True},
             "swaps_accepted": int((after["swaps_accepted"] - before["swaps_accepted"]).sum()),
             "config": {"workload": desc}, "clocks": clk.summary()}
     s.close()

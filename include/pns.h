@@ -136,7 +136,8 @@ typedef struct {
     int32_t team_warps;        /* warps evaluating the chain's candidates (non-speculative kernel) */
     int32_t producer_warps;    /* warps precomputing the next record's random numbers */
     int32_t spec_depth;        /* speculative kernel: records evaluated at once (0: not used) */
-    int32_t reserved;
+    int32_t period_blocked;    /* 1: period-blocked update (Unbiased PNS with exchange): set fields
+                                  from the k x k sub-block, other fields once per period */
 } pns_info;
 
 typedef struct {

@@ -62,6 +62,7 @@ struct pns_ctx {
     pns_config cfg{};
     int fmt = 0, qtype = 0, is_float = 0, hbytes = 4, T = 1, prod = 0;
     int spec = 0;  // > 0: speculative kernel with this many warps (records) per chain
+    bool blocked = false;  // period-blocked kernel
     std::vector<InstHost> inst;
     int32_t max_ld = 32, LD = 32, W = 1;
     int64_t chains = 0;
@@ -87,7 +88,7 @@ struct pns_ctx {
     int64_t tape_alloc = 0;  // records per chain allocated
     int64_t tape_cap = 0;    // records per chain of the last run
     // plan
-    int n_cta = 0, block = 32;
+    int n_cta = 0, n_threads = 32;
     size_t smem = 0;
     int latched = 0;
     std::vector<ChainDesc> h_chains;  // host copy of the chain descriptors (smem offsets per mapping)
@@ -198,6 +199,7 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     const bool team_bars = TT > 32;
     int teams_cap = T == 32 ? 1 : std::min(512 / TT, team_bars ? 7 : 16);
     if (c.spec > 0) teams_cap = std::max(1, std::min(512 / (32 * c.spec), 15));
+    if (c.blocked) teams_cap = 16;
     struct Unit {
         int32_t first, count, bytes;
     };
@@ -205,12 +207,73 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     const int R = pt ? c.R : 1;
     for (int64_t i = 0; i < c.chains; i += R) {
         const InstHost &ih = c.inst[chains[i].inst];
-        const int32_t per = c.spec > 0 ? spec_chain_bytes(ih.ld, ih.k, c.hbytes, list, c.spec)
-                                       : chain_smem(ih.ld, ih.k, c.hbytes, list, c.prod > 0, slot_list).total;
+        const int32_t per = c.blocked   ? block_chain_bytes(ih.ld, ih.k, c.hbytes, c.qtype == PNS_Q_I16 ? 2 : 4, R)
+                            : c.spec > 0 ? spec_chain_bytes(ih.ld, ih.k, c.hbytes, list, c.spec)
+                                         : chain_smem(ih.ld, ih.k, c.hbytes, list, c.prod > 0, slot_list).total;
         units.push_back({static_cast<int32_t>(i), R, per * R});
     }
     if (R > teams_cap) return fail(PNS_ERR_UNSUPPORTED, "exchange group of %d chains exceeds %d teams per CTA", R, teams_cap);
     std::stable_sort(units.begin(), units.end(), [](const Unit &a, const Unit &b) { return a.bytes > b.bytes; });
+    if (pt && per_cta_override <= 0) {
+        // Exchange groups: as many groups per CTA as the team and barrier
+        // limits allow, and each group (largest first) to the CTA with the
+        // least shared memory so far.  Balanced CTAs keep the launch's
+        // dynamic shared memory (the maximum over CTAs) near the mean, so
+        // that every CTA is resident at once.
+        int cap_units = 0;
+        for (int u = 1; u * R <= teams_cap; ++u) {
+            const int ids = (team_bars ? 2 * u * R : 0) + u;
+            if (ids <= 15) cap_units = u;
+        }
+        if (cap_units == 0) return fail(PNS_ERR_UNSUPPORTED, "an exchange group of %d chains needs too many barriers", R);
+        const int64_t n_cta = (static_cast<int64_t>(units.size()) + cap_units - 1) / cap_units;
+        std::vector<std::vector<int>> members(n_cta);
+        std::vector<size_t> load(n_cta, 0);
+        for (size_t ui = 0; ui < units.size(); ++ui) {
+            const Unit &u = units[ui];
+            if (static_cast<size_t>(u.bytes) > smem_cap)
+                return fail(PNS_ERR_UNSUPPORTED, "an exchange group needs %d bytes of shared memory, over %zu", u.bytes,
+                            smem_cap);
+            int64_t best = -1;
+            for (int64_t b = 0; b < static_cast<int64_t>(members.size()); ++b) {
+                if (static_cast<int>(members[b].size()) >= cap_units || load[b] + u.bytes > smem_cap) continue;
+                if (best < 0 || load[b] < load[best]) best = b;
+            }
+            if (best < 0) {
+                members.emplace_back();
+                load.push_back(0);
+                best = static_cast<int64_t>(members.size()) - 1;
+            }
+            members[best].push_back(static_cast<int>(ui));
+            load[best] += u.bytes;
+        }
+        out.smem_off.assign(c.chains, 0);
+        int max_teams = 0;
+        for (size_t b = 0; b < members.size(); ++b) {
+            if (members[b].empty()) continue;
+            CtaDesc d;
+            d.first = static_cast<int32_t>(out.cta_chains.size());
+            d.count = 0;
+            d.groups = static_cast<int32_t>(members[b].size());
+            d.pad = 0;
+            size_t off = 0;
+            for (int ui : members[b]) {
+                const Unit &u = units[ui];
+                const int32_t per = u.bytes / u.count;
+                for (int s2 = 0; s2 < u.count; ++s2) {
+                    out.smem_off[u.first + s2] = static_cast<int32_t>(off) + s2 * per;
+                    out.cta_chains.push_back(u.first + s2);
+                }
+                off += u.bytes;
+                d.count += u.count;
+            }
+            out.cta.push_back(d);
+            out.smem = std::max(out.smem, off);
+            max_teams = std::max(max_teams, static_cast<int>(d.count));
+        }
+        out.block = max_teams * (c.blocked ? 32 : TT);
+        return PNS_OK;
+    }
     int64_t target = (static_cast<int64_t>(units.size()) + num_sms - 1) / num_sms;
     if (per_cta_override > 0) target = per_cta_override;
     if (target < 1) target = 1;
@@ -251,9 +314,9 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     close();
     int max_teams = 0;
     for (const CtaDesc &d : out.cta) max_teams = std::max(max_teams, static_cast<int>(d.count));
-    out.block = max_teams * (c.spec > 0 ? 32 * c.spec : TT);
+    out.block = max_teams * (c.spec > 0 ? 32 * c.spec : (c.blocked ? 32 : TT));
     for (const CtaDesc &d : out.cta) {
-        const int ids = c.spec > 0 ? d.count : (team_bars ? 2 * d.count : 0) + (pt ? d.groups : 0);
+        const int ids = c.spec > 0 ? d.count : c.blocked ? d.groups : (team_bars ? 2 * d.count : 0) + (pt ? d.groups : 0);
         if (ids > 15) return fail(PNS_ERR_UNSUPPORTED, "a CTA needs %d named barriers (15 available)", ids);
     }
     return PNS_OK;
@@ -278,8 +341,16 @@ static int auto_warps(const pns_ctx &c) {
 
 // A chain-to-CTA mapping: warps per chain, producer warps, speculation depth.
 struct Mapping {
-    int T = 1, prod = 0, spec = 0, per_cta = 0;
+    int T = 1, prod = 0, spec = 0, per_cta = 0, block = 0;
 };
+
+// The period-blocked kernel: Unbiased PNS, systematic sets, exchange, dense Q, k <= 128.
+static bool block_allowed(const pns_ctx &c) {
+    int kmax = 1;
+    for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
+    return c.fmt == PNS_DENSE && c.cfg.swap_interval > 0 && c.cfg.variant == PNS_UNBIASED &&
+           c.cfg.subset == PNS_SUBSET_SYSTEMATIC && block_supported(c.qtype, kmax);
+}
 
 static bool spec_allowed(const pns_ctx &c) {
     int kmax = 1;
@@ -322,6 +393,15 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
     }
     if (m.spec > 0 && !spec_allowed(c)) m.spec = 0;
     if (m.spec > 0) m.prod = 0;
+    // Period blocking (dependent row loads off the record chain of every
+    // exchange group) is chosen by the autotuner or PNS_BLOCKED.
+    m.block = 0;
+    if (const char *e = getenv("PNS_BLOCKED")) m.block = atoi(e) && block_allowed(c) ? 1 : 0;
+    if (m.block) {
+        m.T = 1;
+        m.prod = 0;
+        m.spec = 0;
+    }
     return PNS_OK;
 }
 
@@ -335,6 +415,7 @@ static pns_status apply_mapping(pns_ctx *c, Mapping m, cudaStream_t s) {
         c->T = m.T;
         c->prod = m.prod;
         c->spec = m.spec;
+        c->blocked = m.block != 0;
         pl = PlanOut();
         st = plan(*c, c->h_chains, c->num_sms, static_cast<size_t>(c->smem_optin), m.per_cta, pl);
         if (st == PNS_OK || m.prod == 0) break;
@@ -350,7 +431,7 @@ static pns_status apply_mapping(pns_ctx *c, Mapping m, cudaStream_t s) {
     c->d_cta = nullptr;
     c->d_cta_chains = nullptr;
     c->n_cta = static_cast<int>(pl.cta.size());
-    c->block = pl.block;
+    c->n_threads = pl.block;
     c->smem = pl.smem;
     CU(cudaMalloc(&c->d_chain, sizeof(ChainDesc) * chains.size()));
     CU(cudaMemcpyAsync(c->d_chain, chains.data(), sizeof(ChainDesc) * chains.size(), cudaMemcpyHostToDevice, s));
@@ -399,7 +480,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
                 if (!bar) continue;
                 if (std::string(line, bar - line) == key) {
                     Mapping m;
-                    if (sscanf(bar + 1, "%d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta) == 4) {
+                    if (sscanf(bar + 1, "%d %d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta, &m.block) == 5) {
                         fclose(f);
                         return apply_mapping(c, m, s);
                     }
@@ -420,8 +501,10 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         if (T_fixed > 0 && (m.T != T_fixed || m.spec > 0)) return;
         if (!sampler_supported(c->fmt, c->qtype, c->hbytes, m.T)) return;
         if (m.spec > 0 && (!spec_allowed(*c) || !spec_supported(c->qtype, m.spec))) return;
+        if (m.block && (!block_allowed(*c) || m.T != 1)) return;
         for (const Mapping &o : cands)
-            if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta) return;
+            if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta && o.block == m.block)
+                return;
         cands.push_back(m);
     };
     if (c->fmt == PNS_DENSE) {
@@ -429,6 +512,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
             for (int prod = 0; prod <= 3; ++prod) add(Mapping{T, prod, 0, c->per_cta});
         add(Mapping{8, 0, 0, c->per_cta});
         for (int d : {4, 8, 16}) add(Mapping{1, 0, d, c->per_cta});
+        add(Mapping{1, 0, 0, c->per_cta, 1});
     } else {
         for (int T : Ts_csr) add(Mapping{T, 0, 0, c->per_cta});
     }
@@ -502,7 +586,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
     if (code != 0) return fail(static_cast<pns_status>(code), "device error while autotuning");
     if (path) {
         if (FILE *f = fopen(path, "a")) {
-            fprintf(f, "%s|%d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta);
+            fprintf(f, "%s|%d %d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta, best.block);
             fclose(f);
         }
     }
@@ -528,7 +612,7 @@ pns_status pns_get_info(const pns_ctx *ctx, pns_info *info) {
     info->team_warps = ctx->spec > 0 ? 0 : ctx->T;
     info->producer_warps = ctx->spec > 0 ? 0 : ctx->prod;
     info->spec_depth = ctx->spec;
-    info->reserved = 0;
+    info->period_blocked = ctx->blocked ? 1 : 0;
     return PNS_OK;
 }
 
@@ -860,8 +944,9 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.chain_base = static_cast<uint32_t>(c->cfg.chain_base);
     P.group_base = static_cast<uint32_t>(c->cfg.group_base);
     auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {
-        if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->block, c->smem, s);
-        return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->block, c->smem, s);
+        if (c->blocked) return launch_block(c->qtype, Pl, grid, c->n_threads, c->smem, s);
+        if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->n_threads, c->smem, s);
+        return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->n_threads, c->smem, s);
     };
     if (!plain && c->cfg.graph && s != nullptr && !c->tape_off) {
         // one captured launch per step count; the chain state lives in device

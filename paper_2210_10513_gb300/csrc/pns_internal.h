@@ -19,7 +19,7 @@ enum : int { SUB_SYSTEMATIC = 0, SUB_RANDOM = 1 };
 enum : uint32_t { TAG_RACE = 1, TAG_STEP = 2, TAG_SUBSET = 3, TAG_SWAP = 5 };
 
 // Device status codes (mirror pns_status values).
-enum : int { ST_OK = 0, ST_TIMEOUT = 6 };
+enum : int { ST_OK = 0, ST_TIMEOUT = 6, ST_STATE = 7 };
 
 // One QUBO instance as the kernels see it.
 struct InstDesc {
@@ -112,6 +112,31 @@ PNS_HD ChainSmem chain_smem(int32_t ld, int32_t k, int32_t hbytes, bool list, bo
     s.slot_bytes = slots ? round16(16 + 4 * k + (slot_list ? 4 * k : 0)) : 0;
     s.scratch = s.slots + 2 * s.slot_bytes;
     s.total = s.scratch + 768;   // 5 partials x 32 warps x 4 B, then publish / control words
+    return s;
+}
+
+// Period-blocked kernel (Unbiased PNS, systematic sets, exchange groups).
+// A chain's fields stay in global memory; shared memory holds the k fields
+// of its current set, its bits, a log of the period's flips and a few control
+// words.  The group's k x k sub-block Q[N_i, N_i] and the set's b and
+// diagonal follow the R chain areas.  The host gives every chain of a group
+// ceil(group_bytes / R) bytes.
+constexpr int BLOCK_LOG = 128;  // flips logged before a chain applies them itself
+
+struct BlockSmem {
+    int32_t insf, xw, log, scratch, chain_bytes, sub, bd, group_bytes;
+};
+
+PNS_HD BlockSmem block_smem(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R) {
+    BlockSmem s;
+    s.insf = 0;
+    s.xw = round16(k * hbytes);
+    s.log = s.xw + round16(ld / 8);
+    s.scratch = s.log + 4 * BLOCK_LOG;
+    s.chain_bytes = s.scratch + 32;  // E, beta index, swap count, set start, log length
+    s.sub = R * s.chain_bytes;
+    s.bd = s.sub + round16(k * k * qbytes);  // b and diag of the set, 4-byte entries
+    s.group_bytes = s.bd + round16(8 * k);
     return s;
 }
 

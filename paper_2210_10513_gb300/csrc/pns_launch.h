@@ -44,6 +44,13 @@ bool spec_supported(int qtype, int D);
 cudaError_t launch_spec(int qtype, int D, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
 int32_t spec_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, bool list, int32_t D);
 
+// Period-blocked kernel for Unbiased PNS with systematic sets and replica
+// exchange on dense Q (k <= 128): one warp per chain, the group's set
+// sub-block in shared memory, logged rows applied at period ends.
+bool block_supported(int qtype, int k);
+cudaError_t launch_block(int qtype, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
+int32_t block_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R);
+
 // Multiplicity-weighted moments of tape = 2 samples (n <= 64) on tcgen05
 // tensor cores, and gradients assembled from them.
 size_t moments_scratch_bytes(int64_t samples, int n);

@@ -1,0 +1,96 @@
+"""Period-blocked Unbiased PNS with replica exchange: the set fields follow the
+k x k sub-block during a period and the other fields take the logged rows at
+the period end.  Every field receives the same additions in the same order as
+with the per-flip update, so tapes, states, fields and statistics are
+bit-identical to the per-flip kernel (fp32 and integer Q) and to the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2210_10513_gb300 import synth
+from tests.gpu_helpers import gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _probs(ns, qkind, betas, seed=0, kdiv=16, kmin=1):
+    out = []
+    for i, n in enumerate(ns):
+        if qkind == "f32":
+            q = synth.dense_normal(n, 1.0, seed + i)
+        elif qkind == "i16":
+            q = synth.dense_int(n, -100, 100, seed + i, np.int16)
+        else:
+            q = synth.dense_int(n, -20, 20, seed + i, np.int32)
+        out.append(dict(n=n, q=q, b=None, betas=betas, k=max(kmin, n // kdiv)))
+    return out
+
+
+def _pair(monkeypatch, probs, steps, **cfg):
+    monkeypatch.setenv("PNS_BLOCKED", "1")
+    a = gpu_run(probs, steps, tape=True, **cfg)
+    monkeypatch.setenv("PNS_BLOCKED", "0")
+    b = gpu_run(probs, steps, tape=True, **cfg)
+    monkeypatch.delenv("PNS_BLOCKED")
+    assert a["info"].period_blocked == 1 and b["info"].period_blocked == 0
+    np.testing.assert_array_equal(a["stats"], b["stats"])
+    np.testing.assert_array_equal(a["states"], b["states"])
+    np.testing.assert_array_equal(a["fields"], b["fields"])
+    for cid, rec in enumerate(a["stats"]["tape_records"]):
+        np.testing.assert_array_equal(a["flips"][cid, :rec], b["flips"][cid, :rec])
+        np.testing.assert_array_equal(a["m"][cid, :rec], b["m"][cid, :rec])
+    return a
+
+
+@pytest.mark.parametrize("qkind", ["f32", "i16", "i32"])
+def test_blocked_equals_per_flip(monkeypatch, qkind):
+    betas = synth.geometric_ladder(0.1, 10.0, 8)
+    probs = _probs([130, 257, 96, 2048], qkind, betas, seed=4)
+    g = _pair(monkeypatch, probs, 2000, variant="unbiased", k=1, L0=100, swap_interval=100, seed=8)
+    assert g["stats"]["swaps_accepted"].sum() > 0
+
+
+def test_blocked_long_periods_flush_the_log(monkeypatch):
+    """L0 = 1000 at hot temperatures: more than 128 moves in a period, so the
+    chain applies its full log itself in the middle of the period."""
+    betas = synth.geometric_ladder(0.01, 0.05, 4)
+    probs = _probs([200, 333], "f32", betas, seed=6)
+    g = _pair(monkeypatch, probs, 4000, variant="unbiased", k=1, L0=1000, swap_interval=2000, seed=3)
+    m = g["m"]
+    assert (g["stats"]["flips"] > 300).all()
+    assert g["stats"]["tape_records"].max() > 2 * 128
+    assert np.isfinite(m).all()
+
+
+@pytest.mark.parametrize("n,k", [(128, 128), (100, 1), (97, 13), (64, 40)])
+def test_blocked_set_shapes(monkeypatch, n, k):
+    """Whole-set windows, single-bit sets and windows that wrap around n."""
+    betas = synth.geometric_ladder(0.2, 3.0, 3)
+    q = synth.dense_int(n, -30, 30, n, np.int32)
+    probs = [dict(n=n, q=q, b=synth.vector_int(n, -30, 30, n, np.int32), betas=betas, k=k)]
+    _pair(monkeypatch, probs, 1500, variant="unbiased", k=1, L0=50, swap_interval=150, seed=n,
+          chains_per_replica=2)
+
+
+def test_blocked_matches_oracle(monkeypatch):
+    monkeypatch.setenv("PNS_BLOCKED", "1")
+    ns = [130, 97]
+    betas = synth.geometric_ladder(0.1, 10.0, 4)
+    probs = _probs(ns, "f32", betas, seed=9, kdiv=8)
+    L0, swap, steps = 100, 200, 2000
+    g = gpu_run(probs, steps, tape=True, variant="unbiased", k=1, L0=L0, swap_interval=swap, seed=17)
+    assert g["info"].period_blocked == 1
+    R = len(betas)
+    for p, pr in enumerate(probs):
+        res = O.run_tempering(O.Problem(q=pr["q"]), betas, dict(variant="unbiased", k=pr["k"], L0=L0, seed=17),
+                              group_id=p, chain_id0=p * R, x0s=[np.zeros(pr["n"], np.uint8)] * R,
+                              rounds=steps // swap, periods_per_round=swap // L0)
+        for s in range(R):
+            cid = p * R + s
+            rec = int(g["stats"]["tape_records"][cid])
+            assert rec == len(res[s]["flips"])
+            np.testing.assert_array_equal(g["flips"][cid, :rec], res[s]["flips"])
+            np.testing.assert_array_equal(g["m"][cid, :rec], res[s]["m"])
+            assert g["stats"][cid]["energy"] == res[s]["state"].E
+            bits = synth.unpack_bits(g["states"][cid:cid + 1], pr["n"])[0]
+            np.testing.assert_array_equal(bits, res[s]["x"])

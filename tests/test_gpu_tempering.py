@@ -21,9 +21,11 @@ def _problems(ns, seed=0, integer=False):
     return probs
 
 
-@pytest.mark.parametrize("integer,prefetch", [(False, "0"), (True, "0"), (False, "1")])
-def test_unbiased_tempering_matches_oracle(monkeypatch, integer, prefetch):
+@pytest.mark.parametrize("integer,prefetch,blocked", [(False, "0", "1"), (True, "0", "1"), (False, "0", "0"),
+                                                      (True, "0", "0"), (False, "1", "0")])
+def test_unbiased_tempering_matches_oracle(monkeypatch, integer, prefetch, blocked):
     monkeypatch.setenv("PNS_PREFETCH", prefetch)
+    monkeypatch.setenv("PNS_BLOCKED", blocked)
     ns = [130, 257, 96]
     betas = synth.geometric_ladder(0.1, 10.0, 4)
     probs = _problems(ns, seed=3, integer=integer)

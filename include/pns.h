@@ -133,7 +133,8 @@ typedef struct {
     int64_t tape_capacity;     /* records per chain held by the tape of the last pns_run */
     int32_t warps_per_chain;   /* mapping in use: warps that serve one chain (all kinds) */
     int32_t ctas;              /* CTAs of the sampling launch */
-    int32_t team_warps;        /* warps evaluating the chain's candidates (non-speculative kernel) */
+    int32_t team_warps;        /* warps evaluating the chain's candidates (non-speculative kernel);
+                                  period-blocked kernel: warps serving one exchange group */
     int32_t producer_warps;    /* warps precomputing the next record's random numbers */
     int32_t spec_depth;        /* speculative kernel: records evaluated at once (0: not used) */
     int32_t period_blocked;    /* 1: period-blocked update (Unbiased PNS with exchange): set fields

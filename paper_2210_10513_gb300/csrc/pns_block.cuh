@@ -4,25 +4,29 @@
 // only bits of its current systematic set N_i, so only the k fields of N_i are
 // ever read.  This kernel keeps those k fields in shared memory, current from
 // the k x k sub-block Q[N_i, N_i], and logs the period's flips; every other
-// field (in global memory) receives the logged rows at the period end, when
-// all rows are known and can be loaded together instead of one dependent row
-// load per flip.  Each field still receives the same IEEE additions in the
-// same order as with the per-flip update (h_r += s_j Q_rj over the flips j in
-// time order), so fields, energies and records are bit-identical to the
-// per-flip kernel for integer and fp32 QUBOs alike.
+// field (in global memory) receives the logged rows once the chain's period is
+// over, when all rows are known and can be loaded together instead of one
+// dependent row load per flip.  Each field still receives the same IEEE
+// additions in the same order as with the per-flip update (h_r += s_j Q_rj
+// over the flips j in time order), so fields, energies and records are
+// bit-identical to the per-flip kernel for integer and fp32 QUBOs alike.
 //
 // The replicas of an exchange group move through the same systematic sets
 // (each completes one period per L0 original samples and the group meets at
-// every period end), so one sub-block serves the whole group.  Per period:
-//   records   each chain (one warp) runs its records to the period end; a
-//             move updates the k set fields from the sub-block and appends
-//             (j, direction) to the chain's log
+// every period end), so one sub-block serves the whole group.  A group of R
+// chains is served by W <= R warps.  Per period:
+//   records   the warps take the group's chains from a queue, hottest first
+//             (ordered by the records each temperature took in the previous
+//             period), and run each to its period end; a move updates the k
+//             set fields from the sub-block, appends (j, direction) to the
+//             chain's log and prefetches row j into L2
+//   finalise  a warp that ends a chain while others still run applies that
+//             chain's log to its fields outside N_i and gathers the next
+//             set's fields; the chain that ends last is finalised by the
+//             whole group
 //   exchange  at round ends adjacent temperatures swap, as in the per-flip
 //             kernel (same random numbers and arithmetic)
-//   apply     the group applies every chain's log to its fields outside N_i
-//             (16-byte row chunks, APPLY_U rows in flight per thread) and
-//             gathers the next set's fields, while the next sub-block arrives
-//             by cp.async
+// while the next set's sub-block arrives by cp.async.
 #pragma once
 
 #include "pns_sampler.cuh"
@@ -52,7 +56,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // of the window [s_next, s_next + k) into insf (the next set's fields).  A
 // log entry is the flipped bit j, with the sign bit set for a 0 -> 1 flip.
 template <typename QT, typename HT>
-__device__ __forceinline__ void apply_item(const QT *Q, int ld, HT *hg, const int32_t *log, int len, int q,
+__device__ __noinline__ void apply_item(const QT *Q, int ld, HT *hg, const int32_t *log, int len, int q,
                                            int s_prev, int s_next, int k, int n, HT *insf) {
     constexpr int VE = 16 / static_cast<int>(sizeof(QT));
     const int r0 = q * VE;
@@ -114,6 +118,10 @@ __device__ __forceinline__ void apply_item(const QT *Q, int ld, HT *hg, const in
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename QT, typename HT>
 __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
     using A = Arith<HT>;
@@ -123,72 +131,87 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
 
     extern __shared__ __align__(16) unsigned char smem[];
     const CtaDesc cd = P.cta[blockIdx.x];
-    const int team = threadIdx.x >> 5;
-    if (team >= cd.count) return;  // idle warps take part in no barrier
-    const int lane = threadIdx.x & 31;
+    const int W = P.gw;
     const int R = P.R;
-    const int pos = team % R;  // position inside the exchange group
-    const int cid = P.cta_chains[cd.first + team];
-    const ChainDesc chd = P.chain[cid];
-    const InstDesc in = P.inst[chd.inst];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = warp / W;
+    if (g >= cd.groups) return;  // idle warps take part in no barrier
+    const int wg = warp - g * W;
+    const int gtid = wg * 32 + lane;
+    const int GT = 32 * W;
+    const int c0 = cd.first + g * R;  // the group's chains: cta_chains[c0 .. c0 + R)
+    const ChainDesc chd0 = P.chain[P.cta_chains[c0]];
+    const InstDesc in = P.inst[chd0.inst];
     const int n = in.n;
     const int ld = in.ld;
     const int k = in.k;
     const QT *Q = reinterpret_cast<const QT *>(in.q);
     const BlockSmem L = block_smem(ld, k, static_cast<int32_t>(sizeof(HT)), static_cast<int32_t>(sizeof(QT)), R);
-    unsigned char *gbase = smem + P.chain[P.cta_chains[cd.first + team - pos]].smem_off;
-    auto area = [&](int p) { return gbase + p * L.chain_bytes; };
-    unsigned char *base = area(pos);
-    HT *insf = reinterpret_cast<HT *>(base + L.insf);  // fields of the current set, position t
-    HT *const hg = reinterpret_cast<HT *>(P.fields) + static_cast<int64_t>(cid) * P.LD;
-    uint32_t *xw = reinterpret_cast<uint32_t *>(base + L.xw);
-    int32_t *log = reinterpret_cast<int32_t *>(base + L.log);
-    double *pub_E = reinterpret_cast<double *>(base + L.scratch);
-    int32_t *pub_b = reinterpret_cast<int32_t *>(base + L.scratch + 8);
-    int32_t *swap_cnt = reinterpret_cast<int32_t *>(base + L.scratch + 12);
-    int32_t *pub_set = reinterpret_cast<int32_t *>(base + L.scratch + 16);
-    int32_t *pub_len = reinterpret_cast<int32_t *>(base + L.scratch + 20);
+    unsigned char *gbase = smem + chd0.smem_off;
+    auto area = [&](int s) { return gbase + s * L.chain_bytes; };
+    auto cst = [&](int s) { return reinterpret_cast<ChainState *>(area(s) + L.state); };
+    auto sc32 = [&](int s, int off) { return reinterpret_cast<int32_t *>(area(s) + L.scratch + off); };
+    auto step0_of = [&](int s) { return reinterpret_cast<int64_t *>(area(s) + L.scratch + 16); };
+    auto cid_of = [&](int s) { return P.cta_chains[c0 + s]; };
+    auto hg_of = [&](int s) { return reinterpret_cast<HT *>(P.fields) + static_cast<int64_t>(cid_of(s)) * P.LD; };
+    // scratch words: 0 log length, 4 records this period, 8 finalised, 12 set start
     QT *sub = reinterpret_cast<QT *>(gbase + L.sub);
     CT *sub_b = reinterpret_cast<CT *>(gbase + L.bd);
-    CT *sub_d = sub_b + k;
+    CT *sub_d = reinterpret_cast<CT *>(gbase + L.bd + round16(4 * k));
+    int32_t *q_order = reinterpret_cast<int32_t *>(gbase + L.ctrl);
+    int32_t *q_next = q_order + 16;
+    int32_t *q_running = q_order + 17;
     const CT *bvec = reinterpret_cast<const CT *>(in.b);
     const CT *dvec = reinterpret_cast<const CT *>(in.diag);
+    const uint64_t seed = P.seed;
+    const uint32_t row_bytes = static_cast<uint32_t>(ld) * static_cast<uint32_t>(sizeof(QT));
 
     // one named barrier per exchange group (id 0 is __syncthreads')
-    const int gbar = 1 + team / R;
-    const int GT = 32 * R;
-    const int gtid = pos * 32 + lane;
+    const int gbar = 1 + g;
     auto gsync = [&]() { named_sync(gbar, GT); };
 
-    // ---- load the chain ------------------------------------------------------
-    ChainState st = P.state[cid];
-    {
+    // ---- load the group's chains ------------------------------------------------
+    for (int s = wg; s < R; s += W) {
+        const int cid = cid_of(s);
+        const ChainState st = P.state[cid];
         const uint32_t *gx = P.xbits + static_cast<int64_t>(cid) * P.W;
+        uint32_t *xw = reinterpret_cast<uint32_t *>(area(s) + L.xw);
+        HT *insf = reinterpret_cast<HT *>(area(s) + L.insf);
+        const HT *hg = hg_of(s);
         for (int w = lane; w < ld / 32; w += 32) xw[w] = gx[w];
         for (int t = lane; t < k; t += 32) {
             int r = st.set_start + t;
             if (r >= n) r -= n;
             insf[t] = hg[r];
         }
-    }
-    const uint64_t seed = P.seed;
-    const uint32_t chain_id = static_cast<uint32_t>(cid) + P.chain_base;
-    float beta = in.betas[st.beta_idx];
-    if (lane == 0) {
-        *swap_cnt = 0;
-        *pub_set = st.set_start;
+        if (lane == 0) {
+            *cst(s) = st;
+            *sc32(s, 12) = st.set_start;
+            *step0_of(s) = st.step;
+        }
     }
     gsync();
     // every replica of the group must stand at the same systematic set
+    int s0 = *sc32(0, 12);
     bool bad = false;
-    for (int p = 0; p < R; ++p) bad |= *reinterpret_cast<const int32_t *>(area(p) + L.scratch + 16) != st.set_start;
-    bad = __any_sync(0xFFFFFFFFu, bad);
-    // (the flag is the same for all warps of the group: they compare the same words)
+    for (int s = 1; s < R; ++s) bad |= *sc32(s, 12) != s0;
     if (bad && gtid == 0) set_status(P.status, ST_STATE);
-    int s0 = st.set_start;
+    if (gtid == 0) {
+        // first queue: hottest temperature first
+        for (int s = 0; s < R; ++s) q_order[s] = s;
+        for (int a = 1; a < R; ++a)
+            for (int b = a; b > 0 && cst(q_order[b])->beta_idx < cst(q_order[b - 1])->beta_idx; --b) {
+                const int t = q_order[b];
+                q_order[b] = q_order[b - 1];
+                q_order[b - 1] = t;
+            }
+        *q_next = 0;
+        *q_running = R;
+    }
 
-    // The next set's sub-block, b and diagonal, by cp.async (4-byte entries)
-    // or plain loads (2-byte entries).
+    // The set's sub-block, b and diagonal, by cp.async (4-byte entries) or
+    // plain loads (2-byte entries).
     auto load_set = [&](int s) {
         const int kk = k * k;
         for (int idx = gtid; idx < kk; idx += GT) {
@@ -209,159 +232,206 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
         }
     };
 
-    // Every chain's log of the period, applied to its fields outside
-    // [s, s + k); then the fields of the next set [sn, sn + k) are gathered
-    // into the chains' set buffers (unless this was the last period).
-    auto apply_group = [&](int s, int sn, bool last) {
-        const int nch = ld / VE;
-        const int total = R * nch;
-        for (int it = gtid; it < total; it += GT) {
-            const int c = it / nch, q = it - c * nch;
-            unsigned char *b = area(c);
-            const int len = *reinterpret_cast<const int32_t *>(b + L.scratch + 20);
-            const int cc = P.cta_chains[cd.first + team - pos + c];
-            apply_item<QT, HT>(Q, ld, reinterpret_cast<HT *>(P.fields) + static_cast<int64_t>(cc) * P.LD,
-                               reinterpret_cast<const int32_t *>(b + L.log), len, q, s, sn, k, n,
-                               last ? nullptr : reinterpret_cast<HT *>(b + L.insf));
-        }
-    };
-
-    // ---- records ---------------------------------------------------------------
-    int64_t tape_pos = 0;
-    int32_t pend_flip = 0;
-    double pend_m = 0.0;
-    bool pend = false;
-    auto flush_record = [&]() {
-        if (pend) {
-            if (lane == 0 && P.tape >= 1 && tape_pos < P.tape_cap) {
-                const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos;
-                P.tape_flip[o] = pend_flip;
-                P.tape_m[o] = pend_m;
+    // ---- one chain's period (one warp) -----------------------------------------
+    auto run_period = [&](int s) {
+        const int cid = cid_of(s);
+        const uint32_t chain_id = static_cast<uint32_t>(cid) + P.chain_base;
+        HT *insf = reinterpret_cast<HT *>(area(s) + L.insf);
+        uint32_t *xw = reinterpret_cast<uint32_t *>(area(s) + L.xw);
+        int32_t *log = reinterpret_cast<int32_t *>(area(s) + L.log);
+        HT *const hg = hg_of(s);
+        ChainState st = *cst(s);
+        const int64_t step0 = *step0_of(s);
+        const float beta = in.betas[st.beta_idx];
+        int len = 0, nrec = 0;
+        // The state-independent draws of a record (race exponentials of the
+        // lane's four positions, the multiplicity's Exp(1)), computed one
+        // record ahead so that they fill the stalls of the current record's
+        // dependent chain.
+        float ex[4], e1;
+        auto draws = [&](uint64_t step, float *x, float &e) {
+            const uint4 rw = 4 * lane < k ? rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(lane))
+                                          : make_uint4(0u, 0u, 0u, 0u);
+            x[0] = race_exp(rw.x);
+            x[1] = race_exp(rw.y);
+            x[2] = race_exp(rw.z);
+            x[3] = race_exp(rw.w);
+            e = record_draws(seed, chain_id, step, n, false, true).e1;
+        };
+        draws(static_cast<uint64_t>(st.step), ex, e1);
+        // deferred tape entry (written one record late)
+        int32_t pend_flip = 0;
+        double pend_m = 0.0;
+        int64_t pend_pos = -1;
+        // (the fp64 sum of M and the running minimum of E are also taken one
+        // record late, when their operands are long ready)
+        auto flush_record = [&]() {
+            if (pend_pos >= 0) {
+                if (lane == 0 && P.tape >= 1 && pend_pos < P.tape_cap) {
+                    const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + pend_pos;
+                    P.tape_flip[o] = pend_flip;
+                    P.tape_m[o] = pend_m;
+                }
+                st.sum_m = __dadd_rn(st.sum_m, pend_m);
+                st.best_E = fmin(st.best_E, st.E);
             }
-            tape_pos += 1;
-            pend = false;
-        }
-    };
-    auto write_record = [&](int32_t flip, double m) {
-        flush_record();
-        pend_flip = flip;
-        pend_m = m;
-        pend = true;
-        st.sum_m = __dadd_rn(st.sum_m, m);
-    };
-    int64_t rec_started = 0;
-    auto sample_record = [&]() {
-        if (P.tape == 2 && rec_started < P.tape_cap) {
-            const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + rec_started;
-            uint32_t *tx = P.tape_x + o * P.W;
-            for (int q = lane; q < P.W; q += 32) tx[q] = q < ld / 32 ? xw[q] : 0u;
-            if (lane == 0) P.tape_E[o] = st.E;
-        }
-        rec_started += 1;
-    };
-
-    int len = 0;  // entries in this chain's log
-    // Set position t -> bit.
-    auto bit_of = [&](int t) {
-        const int i = s0 + t;
-        return i >= n ? i - n : i;
-    };
-    auto delta_t = [&](int t, int i) -> D {
-        const bool xi = (xw[i >> 5] >> (i & 31)) & 1u;
-        return A::delta(insf[t], sub_b[t], sub_d[t], xi);
-    };
-
-    // One record of Unbiased PNS on the set at s0; true at the period end.
-    // Lane l evaluates positions 4l .. 4l + 3 (k <= 128), whose race words
-    // are the four words of Philox block l.
-    auto one_record = [&]() -> bool {
-        sample_record();
-        const uint64_t step = static_cast<uint64_t>(st.step);
-        const RecordDraws rd = record_draws(seed, chain_id, step, n, false, true);
-        const int t0 = 4 * lane;
-        D dl[4];
-        uint32_t lmin = 0xFFFFFFFFu;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int t = t0 + u;
-            if (t < k) {
-                dl[u] = delta_t(t, bit_of(t));
-                const uint32_t kd = A::key(A::pos(dl[u]));
-                lmin = kd < lmin ? kd : lmin;
-            }
-        }
-        const D amin = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin));
-        const float af = A::tof(amin);
-        const float anchor_f = af > 0.0f ? det_expf(-__fmul_rn(beta, af)) : 1.0f;
-        const uint4 rw = t0 < k ? rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(lane))
-                                : make_uint4(0u, 0u, 0u, 0u);
-        uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int t = t0 + u;
-            if (t < k) {
-                const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u]), amin)));
-                const float ws = __fmul_rn(w, 65536.0f);
-                const float wa = truncf(ws);
-                sa += __float2uint_rz(wa);
-                sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                const uint32_t kb = __float_as_uint(__fdiv_rn(race_exp(pick_word(rw, static_cast<uint32_t>(u))), w));
-                if (kb < bkey) {  // t ascending: the first minimum is kept
-                    bkey = kb;
-                    bpos = static_cast<uint32_t>(t);
+            pend_pos = -1;
+        };
+        auto write_record = [&](int32_t flip, double m) {  // flushed at the start of the next record
+            pend_flip = flip;
+            pend_m = m;
+            pend_pos = st.step - step0;
+        };
+        auto bit_of = [&](int t) {
+            const int i = s0 + t;
+            return i >= n ? i - n : i;
+        };
+        auto delta_t = [&](int t, int i) -> D {
+            const bool xi = (xw[i >> 5] >> (i & 31)) & 1u;
+            return A::delta(insf[t], sub_b[t], sub_d[t], xi);
+        };
+        // One record on the set at s0; true at the period end.  Lane l
+        // evaluates positions 4l .. 4l + 3 (k <= 128), whose race words are
+        // the four words of Philox block l.
+        auto one_record = [&]() -> bool {
+            flush_record();  // the previous record (its E is the state this record starts from)
+            const uint64_t step = static_cast<uint64_t>(st.step);
+            if (P.tape == 2) {
+                const int64_t pos = st.step - step0;
+                if (pos < P.tape_cap) {
+                    const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + pos;
+                    uint32_t *tx = P.tape_x + o * P.W;
+                    for (int q = lane; q < P.W; q += 32) tx[q] = q < ld / 32 ? xw[q] : 0u;
+                    if (lane == 0) P.tape_E[o] = st.E;
                 }
             }
-        }
-        const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
-        const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
-        const uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa);
-        const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
-        const uint64_t S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
-        const int a = static_cast<int>(wpos);
-        const int j = bit_of(a);
-        const Mult mu = multiplicity_e1(S, k, anchor_f, rd.e1);
-        double m = mu.md;
-        const D dj = delta_t(a, j);
-        __syncwarp();
-        bool period_end = false;
-        const bool fits = mu.mi >= 0 ? mu.mi <= st.L : m <= static_cast<double>(st.L);
-        if (fits) {
-            st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(m);
-            if (mu.sat) st.saturated += 1;
-            // the set's fields from the sub-block row of j
-            const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
-            const QT *srow = sub + a * k;
-            for (int t = lane; t < k; t += 32) insf[t] = add_elem<QT, HT>(insf[t], srow[t], up);
-            __syncwarp();
-            if (lane == 0) {
-                xw[j >> 5] ^= 1u << (j & 31);
-                log[len] = j | (up ? static_cast<int32_t>(0x80000000u) : 0);
+            const int t0 = 4 * lane;
+            D dl[4];
+            uint32_t lmin = 0xFFFFFFFFu;
+            if (t0 < k) {
+                // the lane's four positions are contiguous: one 16-byte read per array
+                HT hv[4];
+                CT bv[4], dv[4];
+                *reinterpret_cast<uint4 *>(hv) = *reinterpret_cast<const uint4 *>(insf + t0);
+                *reinterpret_cast<uint4 *>(bv) = *reinterpret_cast<const uint4 *>(sub_b + t0);
+                *reinterpret_cast<uint4 *>(dv) = *reinterpret_cast<const uint4 *>(sub_d + t0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int t = t0 + u;
+                    if (t < k) {
+                        const int i = bit_of(t);
+                        const bool xi = (xw[i >> 5] >> (i & 31)) & 1u;
+                        dl[u] = A::delta(hv[u], bv[u], dv[u], xi);
+                        const uint32_t kd = A::key(A::pos(dl[u]));
+                        lmin = kd < lmin ? kd : lmin;
+                    }
+                }
             }
-            len += 1;
-            st.E = __dadd_rn(st.E, A::tod(dj));
-            st.flips += 1;
-            write_record(j, m);
+            const D amin = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin));
+            const float af = A::tof(amin);
+            const float anchor_f = af > 0.0f ? det_expf(-__fmul_rn(beta, af)) : 1.0f;
+            float exn[4], e1n;
+            draws(step + 1, exn, e1n);
+            uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u;
+                if (t < k) {
+                    const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u]), amin)));
+                    const float ws = __fmul_rn(w, 65536.0f);
+                    const float wa = truncf(ws);
+                    sa += __float2uint_rz(wa);
+                    sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
+                    const uint32_t kb = __float_as_uint(__fdiv_rn(ex[u], w));
+                    if (kb < bkey) {  // t ascending: the first minimum is kept
+                        bkey = kb;
+                        bpos = static_cast<uint32_t>(t);
+                    }
+                }
+            }
+            const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
+            const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
+            const uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa);
+            const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
+            const uint64_t S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
+            const int a = static_cast<int>(wpos);
+            const int j = bit_of(a);
+            const Mult mu = multiplicity_e1(S, k, anchor_f, e1);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ex[u] = exn[u];
+            e1 = e1n;
+            double m = mu.md;
+            const D dj = delta_t(a, j);
             __syncwarp();
-            if (len == BLOCK_LOG) {  // full log: apply it now with this warp
-                const int nch = ld / VE;
-                for (int q = lane; q < nch; q += 32) apply_item<QT, HT>(Q, ld, hg, log, len, q, s0, 0, k, n, nullptr);
+            bool period_end = false;
+            const bool fits = mu.mi >= 0 ? mu.mi <= st.L : m <= static_cast<double>(st.L);
+            if (fits) {
+                st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(m);
+                if (mu.sat) st.saturated += 1;
+                const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
+                if (lane == 0) prefetch_l2(Q + static_cast<int64_t>(j) * ld, row_bytes);
+                const QT *srow = sub + a * k;
+                for (int t = lane; t < k; t += 32) insf[t] = add_elem<QT, HT>(insf[t], srow[t], up);
                 __syncwarp();
-                len = 0;
+                if (lane == 0) {
+                    xw[j >> 5] ^= 1u << (j & 31);
+                    log[len] = j | (up ? static_cast<int32_t>(0x80000000u) : 0);
+                }
+                len += 1;
+                st.E = __dadd_rn(st.E, A::tod(dj));
+                st.flips += 1;
+                write_record(j, m);
+                __syncwarp();
+                if (len == BLOCK_LOG) {  // full log: apply it now with this warp
+                    const int nch = ld / VE;
+                    for (int q = lane; q < nch; q += 32)
+                        apply_item<QT, HT>(Q, ld, hg, log, len, q, s0, 0, k, n, nullptr);
+                    __syncwarp();
+                    len = 0;
+                }
+            } else {
+                m = static_cast<double>(st.L);
+                st.L = P.L0;
+                st.stays += 1;
+                int ns = st.set_start + k;
+                while (ns >= n) ns -= n;
+                st.set_start = ns;
+                st.period_start = static_cast<int64_t>(step) + 1;
+                period_end = true;
+                write_record(-1, m);
             }
-        } else {
-            m = static_cast<double>(st.L);
-            st.L = P.L0;
-            st.stays += 1;
-            int ns = st.set_start + k;
-            while (ns >= n) ns -= n;
-            st.set_start = ns;
-            st.period_start = static_cast<int64_t>(step) + 1;
-            period_end = true;
-            write_record(-1, m);
+            st.step += 1;
+            nrec += 1;
+            return period_end;
+        };
+        while (!one_record()) {
         }
-        st.best_E = fmin(st.best_E, st.E);
-        st.step += 1;
-        return period_end;
+        flush_record();
+        __syncwarp();
+        if (lane == 0) {
+            *cst(s) = st;
+            *sc32(s, 0) = len;
+            *sc32(s, 4) = nrec;
+        }
+        __syncwarp();
+    };
+
+    // Chain s after its period, by one warp: its set fields back to global
+    // memory, its log onto the other fields, the next set's fields gathered.
+    auto finalise_warp = [&](int s, int sn, bool last) {
+        HT *insf = reinterpret_cast<HT *>(area(s) + L.insf);
+        HT *const hg = hg_of(s);
+        for (int t = lane; t < k; t += 32) {
+            int r = s0 + t;
+            if (r >= n) r -= n;
+            hg[r] = insf[t];
+        }
+        __syncwarp();
+        const int len = *sc32(s, 0);
+        const int32_t *log = reinterpret_cast<const int32_t *>(area(s) + L.log);
+        const int nch = ld / VE;
+        for (int q = lane; q < nch; q += 32) apply_item<QT, HT>(Q, ld, hg, log, len, q, s0, sn, k, n, last ? nullptr : insf);
+        __syncwarp();
     };
 
     // ---- periods, exchange rounds ------------------------------------------------
@@ -372,75 +442,113 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
     gsync();
     for (int64_t rdi = 0; rdi < rounds; ++rdi) {
         for (int64_t pr = 0; pr < per_round; ++pr) {
-            len = 0;
-            while (!one_record()) {
-            }
-            // the set's fields back to global memory, where the apply step
-            // (other warps of the group) reads whole chunks
-            for (int t = lane; t < k; t += 32) hg[bit_of(t)] = insf[t];
-            if (lane == 0) {
-                *pub_E = st.E;
-                *pub_b = st.beta_idx;
-                *pub_len = len;
+            const bool last = rdi + 1 == rounds && pr + 1 == per_round;
+            int sn = s0 + k;  // the next set (the same for every chain of the group)
+            while (sn >= n) sn -= n;
+            while (true) {
+                int qi = 0;
+                if (lane == 0) qi = atomicAdd(q_next, 1);
+                qi = __shfl_sync(0xFFFFFFFFu, qi, 0);
+                if (qi >= R) break;
+                const int s = q_order[qi];
+                run_period(s);
+                int rem = 0;
+                if (lane == 0) rem = atomicSub(q_running, 1) - 1;
+                rem = __shfl_sync(0xFFFFFFFFu, rem, 0);
+                const bool mine = rem > 0;  // others still run: finalise this chain here
+                if (mine) finalise_warp(s, sn, last);
+                if (lane == 0) *sc32(s, 8) = mine ? 1 : 0;
+                __syncwarp();
             }
             gsync();
-            if (pr + 1 == per_round) {
-                if (pos == 0 && lane == 0) {
-                    const uint64_t ndone = static_cast<uint64_t>(st.sum_m) / static_cast<uint64_t>(P.swap_interval);
+            if (gtid == 0) {
+                // records per temperature in this period, then the exchange
+                int rec_b[16];
+                for (int s = 0; s < R; ++s) rec_b[cst(s)->beta_idx] = *sc32(s, 4);
+                if (pr + 1 == per_round) {
+                    const uint64_t ndone = static_cast<uint64_t>(cst(0)->sum_m) / static_cast<uint64_t>(P.swap_interval);
                     const uint64_t rnd = ndone - 1;
-                    int slot_of[32];
-                    for (int s2 = 0; s2 < R; ++s2) slot_of[*reinterpret_cast<const int32_t *>(area(s2) + L.scratch + 8)] = s2;
+                    int slot_of[16];
+                    for (int s = 0; s < R; ++s) slot_of[cst(s)->beta_idx] = s;
                     int q = 0;
                     for (int a = static_cast<int>(rnd & 1u); a + 1 < R; a += 2, ++q) {
                         const int sa_ = slot_of[a], sb_ = slot_of[a + 1];
-                        unsigned char *pa = area(sa_) + L.scratch;
-                        unsigned char *pb = area(sb_) + L.scratch;
-                        const double Ea = *reinterpret_cast<double *>(pa);
-                        const double Eb = *reinterpret_cast<double *>(pb);
+                        ChainState *pa = cst(sa_);
+                        ChainState *pb = cst(sb_);
                         const float db = __fsub_rn(in.betas[a], in.betas[a + 1]);
-                        const float de = __double2float_rn(__dsub_rn(Ea, Eb));
+                        const float de = __double2float_rn(__dsub_rn(pa->E, pb->E));
                         const float xr = __fmul_rn(db, de);
-                        const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd.group) + P.group_base, rnd,
-                                                    static_cast<uint32_t>(q));
+                        const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd0.group) + P.group_base,
+                                                    rnd, static_cast<uint32_t>(q));
                         if (det_logf(u01_grid(w)) < xr) {
-                            *reinterpret_cast<int32_t *>(pa + 8) = a + 1;
-                            *reinterpret_cast<int32_t *>(pb + 8) = a;
+                            pa->beta_idx = a + 1;
+                            pb->beta_idx = a;
                             slot_of[a] = sb_;
                             slot_of[a + 1] = sa_;
-                            atomicAdd(reinterpret_cast<int32_t *>(pa + 12), 1);
-                            atomicAdd(reinterpret_cast<int32_t *>(pb + 12), 1);
+                            pa->swaps += 1;
+                            pb->swaps += 1;
                         }
                     }
                 }
-                gsync();
-                st.beta_idx = *pub_b;
-                st.swaps += *swap_cnt;
-                __syncwarp();
-                if (lane == 0) *swap_cnt = 0;
-                beta = in.betas[st.beta_idx];
+                // next queue: chains by the records their new temperature took, most first
+                int key[16];
+                for (int s = 0; s < R; ++s) {
+                    key[s] = rec_b[cst(s)->beta_idx];
+                    q_order[s] = s;
+                }
+                for (int a = 1; a < R; ++a)
+                    for (int b = a; b > 0 && key[q_order[b]] > key[q_order[b - 1]]; --b) {
+                        const int t = q_order[b];
+                        q_order[b] = q_order[b - 1];
+                        q_order[b - 1] = t;
+                    }
+                *q_next = 0;
+                *q_running = R;
             }
-            const bool last = rdi + 1 == rounds && pr + 1 == per_round;
-            const int s_next = st.set_start;  // the same for the whole group
-            if (!last) load_set(s_next);      // the sub-block is not read until the next period
-            apply_group(s0, s_next, last);
+            if (!last) load_set(sn);  // the sub-block is not read until the next period
+            // the chain(s) that ended last, by the whole group
+            for (int s = 0; s < R; ++s) {
+                if (*sc32(s, 8)) continue;
+                HT *insf = reinterpret_cast<HT *>(area(s) + L.insf);
+                HT *const hg = hg_of(s);
+                for (int t = gtid; t < k; t += GT) {
+                    int r = s0 + t;
+                    if (r >= n) r -= n;
+                    hg[r] = insf[t];
+                }
+            }
+            gsync();
+            {
+                const int nch = ld / VE;
+                for (int s = 0; s < R; ++s) {
+                    if (*sc32(s, 8)) continue;
+                    HT *insf = reinterpret_cast<HT *>(area(s) + L.insf);
+                    const int len = *sc32(s, 0);
+                    const int32_t *log = reinterpret_cast<const int32_t *>(area(s) + L.log);
+                    HT *const hg = hg_of(s);
+                    for (int q = gtid; q < nch; q += GT)
+                        apply_item<QT, HT>(Q, ld, hg, log, len, q, s0, sn, k, n, last ? nullptr : insf);
+                }
+            }
             cp_async_wait_all();
             gsync();
-            s0 = s_next;
+            s0 = sn;
         }
     }
 
-    // ---- write the chain back ------------------------------------------------------
-    flush_record();
-    __syncwarp();
-    {
-        // (the fields are complete in global memory after the last apply step)
+    // ---- write the chains back ------------------------------------------------------
+    // (the fields are complete in global memory after the last finalise step)
+    for (int s = wg; s < R; s += W) {
+        const int cid = cid_of(s);
+        const uint32_t *xw = reinterpret_cast<const uint32_t *>(area(s) + L.xw);
         uint32_t *gx = P.xbits + static_cast<int64_t>(cid) * P.W;
         for (int w = lane; w < ld / 32; w += 32) gx[w] = xw[w];
-    }
-    if (lane == 0) {
-        st.tape_records = tape_pos < P.tape_cap ? tape_pos : P.tape_cap;
-        if (!P.tape) st.tape_records = 0;
-        P.state[cid] = st;
+        if (lane == 0) {
+            ChainState st = *cst(s);
+            const int64_t recs = st.step - *step0_of(s);
+            st.tape_records = P.tape ? (recs < P.tape_cap ? recs : P.tape_cap) : 0;
+            P.state[cid] = st;
+        }
     }
 }
 

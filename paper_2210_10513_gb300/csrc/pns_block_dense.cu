@@ -24,6 +24,22 @@ cudaError_t launch_block(int qtype, const KParams &P, int grid, int block, size_
     }
 }
 
+int block_occupancy(int qtype, int threads, size_t smem) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    auto query = [&](auto kern) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    };
+    switch (qtype) {
+    case 0: query(pns_block_kernel<int16_t, int32_t>); break;
+    case 1: query(pns_block_kernel<int32_t, int32_t>); break;
+    case 2: query(pns_block_kernel<float, float>); break;
+    default: break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
 int32_t block_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R) {
     const BlockSmem L = block_smem(ld, k, hbytes, qbytes, R);
     return round16((L.group_bytes + R - 1) / R);

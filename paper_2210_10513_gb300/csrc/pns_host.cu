@@ -63,6 +63,7 @@ struct pns_ctx {
     int fmt = 0, qtype = 0, is_float = 0, hbytes = 4, T = 1, prod = 0;
     int spec = 0;  // > 0: speculative kernel with this many warps (records) per chain
     bool blocked = false;  // period-blocked kernel
+    int gw = 1;            // blocked kernel: warps per exchange group
     std::vector<InstHost> inst;
     int32_t max_ld = 32, LD = 32, W = 1;
     int64_t chains = 0;
@@ -182,6 +183,7 @@ struct PlanOut {
     std::vector<int32_t> smem_off;  // per chain
     int block = 32;
     size_t smem = 0;
+    bool resident = true;  // every CTA fits on the GPU at once (blocked kernel: checked)
 };
 
 // Packs chains (or whole exchange groups) into CTAs.  Units are placed in
@@ -215,63 +217,90 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     if (R > teams_cap) return fail(PNS_ERR_UNSUPPORTED, "exchange group of %d chains exceeds %d teams per CTA", R, teams_cap);
     std::stable_sort(units.begin(), units.end(), [](const Unit &a, const Unit &b) { return a.bytes > b.bytes; });
     if (pt && per_cta_override <= 0) {
-        // Exchange groups: as many groups per CTA as the team and barrier
-        // limits allow, and each group (largest first) to the CTA with the
-        // least shared memory so far.  Balanced CTAs keep the launch's
-        // dynamic shared memory (the maximum over CTAs) near the mean, so
-        // that every CTA is resident at once.
+        // Exchange groups: up to cap_u groups per CTA, each group (largest
+        // first) to the CTA with the least shared memory so far.  Balanced
+        // CTAs keep the launch's dynamic shared memory (the maximum over
+        // CTAs) near the mean, so that the CTAs can be resident together.
+        const int wpg = c.blocked ? c.gw : R * (T + c.prod);  // warps per group
         int cap_units = 0;
-        for (int u = 1; u * R <= teams_cap; ++u) {
-            const int ids = (team_bars ? 2 * u * R : 0) + u;
+        const int max_warps = (!c.blocked && T == 32) ? 32 : 16;
+        for (int u = 1; u * wpg <= max_warps; ++u) {
+            const int ids = c.blocked ? u : (team_bars ? 2 * u * R : 0) + u;
             if (ids <= 15) cap_units = u;
         }
-        if (cap_units == 0) return fail(PNS_ERR_UNSUPPORTED, "an exchange group of %d chains needs too many barriers", R);
-        const int64_t n_cta = (static_cast<int64_t>(units.size()) + cap_units - 1) / cap_units;
-        std::vector<std::vector<int>> members(n_cta);
-        std::vector<size_t> load(n_cta, 0);
-        for (size_t ui = 0; ui < units.size(); ++ui) {
-            const Unit &u = units[ui];
+        if (cap_units == 0) return fail(PNS_ERR_UNSUPPORTED, "an exchange group of %d chains needs too many warps or barriers", R);
+        for (const Unit &u : units)
             if (static_cast<size_t>(u.bytes) > smem_cap)
                 return fail(PNS_ERR_UNSUPPORTED, "an exchange group needs %d bytes of shared memory, over %zu", u.bytes,
                             smem_cap);
-            int64_t best = -1;
-            for (int64_t b = 0; b < static_cast<int64_t>(members.size()); ++b) {
-                if (static_cast<int>(members[b].size()) >= cap_units || load[b] + u.bytes > smem_cap) continue;
-                if (best < 0 || load[b] < load[best]) best = b;
-            }
-            if (best < 0) {
-                members.emplace_back();
-                load.push_back(0);
-                best = static_cast<int64_t>(members.size()) - 1;
-            }
-            members[best].push_back(static_cast<int>(ui));
-            load[best] += u.bytes;
-        }
-        out.smem_off.assign(c.chains, 0);
-        int max_teams = 0;
-        for (size_t b = 0; b < members.size(); ++b) {
-            if (members[b].empty()) continue;
-            CtaDesc d;
-            d.first = static_cast<int32_t>(out.cta_chains.size());
-            d.count = 0;
-            d.groups = static_cast<int32_t>(members[b].size());
-            d.pad = 0;
-            size_t off = 0;
-            for (int ui : members[b]) {
+        auto pack = [&](int cap_u, PlanOut &o) {
+            const int64_t n_cta = (static_cast<int64_t>(units.size()) + cap_u - 1) / cap_u;
+            std::vector<std::vector<int>> members(n_cta);
+            std::vector<size_t> load(n_cta, 0);
+            for (size_t ui = 0; ui < units.size(); ++ui) {
                 const Unit &u = units[ui];
-                const int32_t per = u.bytes / u.count;
-                for (int s2 = 0; s2 < u.count; ++s2) {
-                    out.smem_off[u.first + s2] = static_cast<int32_t>(off) + s2 * per;
-                    out.cta_chains.push_back(u.first + s2);
+                int64_t best = -1;
+                for (int64_t b = 0; b < static_cast<int64_t>(members.size()); ++b) {
+                    if (static_cast<int>(members[b].size()) >= cap_u || load[b] + u.bytes > smem_cap) continue;
+                    if (best < 0 || load[b] < load[best]) best = b;
                 }
-                off += u.bytes;
-                d.count += u.count;
+                if (best < 0) {
+                    members.emplace_back();
+                    load.push_back(0);
+                    best = static_cast<int64_t>(members.size()) - 1;
+                }
+                members[best].push_back(static_cast<int>(ui));
+                load[best] += u.bytes;
             }
-            out.cta.push_back(d);
-            out.smem = std::max(out.smem, off);
-            max_teams = std::max(max_teams, static_cast<int>(d.count));
+            o = PlanOut();
+            o.smem_off.assign(c.chains, 0);
+            int max_groups = 0;
+            for (size_t b = 0; b < members.size(); ++b) {
+                if (members[b].empty()) continue;
+                CtaDesc d;
+                d.first = static_cast<int32_t>(o.cta_chains.size());
+                d.count = 0;
+                d.groups = static_cast<int32_t>(members[b].size());
+                d.pad = 0;
+                size_t off = 0;
+                for (int ui : members[b]) {
+                    const Unit &u = units[ui];
+                    const int32_t per = u.bytes / u.count;
+                    for (int s2 = 0; s2 < u.count; ++s2) {
+                        o.smem_off[u.first + s2] = static_cast<int32_t>(off) + s2 * per;
+                        o.cta_chains.push_back(u.first + s2);
+                    }
+                    off += u.bytes;
+                    d.count += u.count;
+                }
+                o.cta.push_back(d);
+                o.smem = std::max(o.smem, off);
+                max_groups = std::max(max_groups, static_cast<int>(d.groups));
+            }
+            o.block = max_groups * 32 * wpg;
+        };
+        if (!c.blocked) {
+            pack(cap_units, out);
+            return PNS_OK;
         }
-        out.block = max_teams * (c.blocked ? 32 : TT);
+        // blocked kernel: the fewest groups per CTA at which every CTA is
+        // resident at once (else the shape with the most resident share)
+        double best_share = -1.0;
+        for (int u = 1; u <= cap_units; ++u) {
+            PlanOut o;
+            pack(u, o);
+            const int occ = block_occupancy(c.qtype, o.block, o.smem);
+            const double share = static_cast<double>(occ) * num_sms / static_cast<double>(o.cta.size());
+            o.resident = share >= 1.0;
+            if (share > best_share) {
+                best_share = share;
+                out = o;
+            }
+            if (o.resident) {
+                out = o;
+                break;
+            }
+        }
         return PNS_OK;
     }
     int64_t target = (static_cast<int64_t>(units.size()) + num_sms - 1) / num_sms;
@@ -341,14 +370,14 @@ static int auto_warps(const pns_ctx &c) {
 
 // A chain-to-CTA mapping: warps per chain, producer warps, speculation depth.
 struct Mapping {
-    int T = 1, prod = 0, spec = 0, per_cta = 0, block = 0;
+    int T = 1, prod = 0, spec = 0, per_cta = 0, block = 0, gw = 0;  // gw 0: chosen by the planner
 };
 
 // The period-blocked kernel: Unbiased PNS, systematic sets, exchange, dense Q, k <= 128.
 static bool block_allowed(const pns_ctx &c) {
     int kmax = 1;
     for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
-    return c.fmt == PNS_DENSE && c.cfg.swap_interval > 0 && c.cfg.variant == PNS_UNBIASED &&
+    return c.fmt == PNS_DENSE && c.cfg.swap_interval > 0 && c.cfg.variant == PNS_UNBIASED && c.R <= 16 &&
            c.cfg.subset == PNS_SUBSET_SYSTEMATIC && block_supported(c.qtype, kmax);
 }
 
@@ -417,6 +446,29 @@ static pns_status apply_mapping(pns_ctx *c, Mapping m, cudaStream_t s) {
         c->spec = m.spec;
         c->blocked = m.block != 0;
         pl = PlanOut();
+        if (c->blocked) {
+            // warps per group: the most (up to R) at which every CTA is resident
+            int gw = m.gw;
+            if (gw == 0)
+                if (const char *e = getenv("PNS_GROUP_WARPS")) gw = atoi(e);
+            if (gw > 0) {
+                c->gw = std::min(gw, c->R);
+                st = plan(*c, c->h_chains, c->num_sms, static_cast<size_t>(c->smem_optin), m.per_cta, pl);
+            } else {
+                st = PNS_ERR_UNSUPPORTED;
+                for (int w = c->R; w >= 1; w = w > 1 ? (w + 1) / 2 : 0) {
+                    c->gw = w;
+                    PlanOut o;
+                    const pns_status s2 = plan(*c, c->h_chains, c->num_sms, static_cast<size_t>(c->smem_optin), m.per_cta, o);
+                    if (s2 != PNS_OK) continue;
+                    st = s2;
+                    pl = o;
+                    if (o.resident) break;
+                    if (w == 1) break;
+                }
+            }
+            break;
+        }
         st = plan(*c, c->h_chains, c->num_sms, static_cast<size_t>(c->smem_optin), m.per_cta, pl);
         if (st == PNS_OK || m.prod == 0) break;
         m.prod -= 1;
@@ -480,7 +532,8 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
                 if (!bar) continue;
                 if (std::string(line, bar - line) == key) {
                     Mapping m;
-                    if (sscanf(bar + 1, "%d %d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta, &m.block) == 5) {
+                    if (sscanf(bar + 1, "%d %d %d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta, &m.block, &m.gw) ==
+                        6) {
                         fclose(f);
                         return apply_mapping(c, m, s);
                     }
@@ -503,7 +556,8 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         if (m.spec > 0 && (!spec_allowed(*c) || !spec_supported(c->qtype, m.spec))) return;
         if (m.block && (!block_allowed(*c) || m.T != 1)) return;
         for (const Mapping &o : cands)
-            if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta && o.block == m.block)
+            if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta && o.block == m.block &&
+                o.gw == m.gw)
                 return;
         cands.push_back(m);
     };
@@ -512,7 +566,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
             for (int prod = 0; prod <= 3; ++prod) add(Mapping{T, prod, 0, c->per_cta});
         add(Mapping{8, 0, 0, c->per_cta});
         for (int d : {4, 8, 16}) add(Mapping{1, 0, d, c->per_cta});
-        add(Mapping{1, 0, 0, c->per_cta, 1});
+        for (int gw : {0, c->R, (c->R + 1) / 2, (c->R + 3) / 4}) add(Mapping{1, 0, 0, c->per_cta, 1, gw});
     } else {
         for (int T : Ts_csr) add(Mapping{T, 0, 0, c->per_cta});
     }
@@ -586,7 +640,8 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
     if (code != 0) return fail(static_cast<pns_status>(code), "device error while autotuning");
     if (path) {
         if (FILE *f = fopen(path, "a")) {
-            fprintf(f, "%s|%d %d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta, best.block);
+            fprintf(f, "%s|%d %d %d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta, best.block,
+                    best.gw);
             fclose(f);
         }
     }
@@ -609,7 +664,7 @@ pns_status pns_get_info(const pns_ctx *ctx, pns_info *info) {
     info->tape_capacity = ctx->tape_cap;
     info->warps_per_chain = ctx->spec > 0 ? ctx->spec : ctx->T + ctx->prod;
     info->ctas = ctx->n_cta;
-    info->team_warps = ctx->spec > 0 ? 0 : ctx->T;
+    info->team_warps = ctx->blocked ? ctx->gw : (ctx->spec > 0 ? 0 : ctx->T);
     info->producer_warps = ctx->spec > 0 ? 0 : ctx->prod;
     info->spec_depth = ctx->spec;
     info->period_blocked = ctx->blocked ? 1 : 0;
@@ -939,6 +994,7 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.tape = c->tape_off ? 0 : c->cfg.tape;
     P.prod = c->prod;
     // speculative row loads for Unbiased PNS when Q does not stay in L2
+    P.gw = c->gw;
     P.prefetch = (c->cfg.variant == PNS_UNBIASED && c->q_bytes > (64ull << 20)) ? 1 : 0;
     if (const char *e = getenv("PNS_PREFETCH")) P.prefetch = atoi(e) ? 1 : 0;
     P.chain_base = static_cast<uint32_t>(c->cfg.chain_base);

@@ -87,7 +87,7 @@ struct KParams {
     uint32_t chain_base;    // global id of chain 0 (Philox stream id = chain_base + chain)
     uint32_t group_base;    // global id of exchange group 0
     int32_t prefetch;       // Unbiased: start the winner's row load before the budget test
-    int32_t pad2;
+    int32_t gw;             // period-blocked kernel: warps per exchange group
 };
 
 PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }
@@ -116,15 +116,15 @@ PNS_HD ChainSmem chain_smem(int32_t ld, int32_t k, int32_t hbytes, bool list, bo
 }
 
 // Period-blocked kernel (Unbiased PNS, systematic sets, exchange groups).
-// A chain's fields stay in global memory; shared memory holds the k fields
-// of its current set, its bits, a log of the period's flips and a few control
-// words.  The group's k x k sub-block Q[N_i, N_i] and the set's b and
-// diagonal follow the R chain areas.  The host gives every chain of a group
-// ceil(group_bytes / R) bytes.
+// A chain's fields stay in global memory; shared memory holds, per chain, the
+// k fields of its current set, its bits, a log of the period's flips, its
+// ChainState and a few control words, and, per group, the k x k sub-block
+// Q[N_i, N_i], the set's b and diagonal and the group's work queue.  The host
+// gives every chain of a group ceil(group_bytes / R) bytes.
 constexpr int BLOCK_LOG = 128;  // flips logged before a chain applies them itself
 
 struct BlockSmem {
-    int32_t insf, xw, log, scratch, chain_bytes, sub, bd, group_bytes;
+    int32_t insf, xw, log, state, scratch, chain_bytes, sub, bd, ctrl, group_bytes;
 };
 
 PNS_HD BlockSmem block_smem(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R) {
@@ -132,11 +132,13 @@ PNS_HD BlockSmem block_smem(int32_t ld, int32_t k, int32_t hbytes, int32_t qbyte
     s.insf = 0;
     s.xw = round16(k * hbytes);
     s.log = s.xw + round16(ld / 8);
-    s.scratch = s.log + 4 * BLOCK_LOG;
-    s.chain_bytes = s.scratch + 32;  // E, beta index, swap count, set start, log length
+    s.state = s.log + 4 * BLOCK_LOG;
+    s.scratch = s.state + static_cast<int32_t>(sizeof(ChainState));
+    s.chain_bytes = s.scratch + 32;  // log length, records, finalised flag, set start, first step
     s.sub = R * s.chain_bytes;
-    s.bd = s.sub + round16(k * k * qbytes);  // b and diag of the set, 4-byte entries
-    s.group_bytes = s.bd + round16(8 * k);
+    s.bd = s.sub + round16(k * k * qbytes);  // b, then diag, of the set: 4-byte entries, 16-byte aligned
+    s.ctrl = s.bd + 2 * round16(4 * k);      // queue order[16], next, running
+    s.group_bytes = s.ctrl + 80;
     return s;
 }
 

@@ -50,6 +50,8 @@ int32_t spec_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, bool list, int32
 bool block_supported(int qtype, int k);
 cudaError_t launch_block(int qtype, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
 int32_t block_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R);
+// CTAs of the blocked kernel resident per SM at this shape (0 on error).
+int block_occupancy(int qtype, int threads, size_t smem);
 
 // Multiplicity-weighted moments of tape = 2 samples (n <= 64) on tcgen05
 // tensor cores, and gradients assembled from them.

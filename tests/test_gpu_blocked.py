@@ -42,8 +42,12 @@ def _pair(monkeypatch, probs, steps, **cfg):
     return a
 
 
-@pytest.mark.parametrize("qkind", ["f32", "i16", "i32"])
-def test_blocked_equals_per_flip(monkeypatch, qkind):
+@pytest.mark.parametrize("qkind,gw", [("f32", "0"), ("i16", "0"), ("i32", "0"), ("f32", "1"), ("f32", "3"),
+                                     ("f32", "8")])
+def test_blocked_equals_per_flip(monkeypatch, qkind, gw):
+    """gw: warps per exchange group (0: the planner's choice); 3 does not
+    divide the 8 replicas."""
+    monkeypatch.setenv("PNS_GROUP_WARPS", gw)
     betas = synth.geometric_ladder(0.1, 10.0, 8)
     probs = _probs([130, 257, 96, 2048], qkind, betas, seed=4)
     g = _pair(monkeypatch, probs, 2000, variant="unbiased", k=1, L0=100, swap_interval=100, seed=8)

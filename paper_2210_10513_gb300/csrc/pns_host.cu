@@ -422,9 +422,9 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
     }
     if (m.spec > 0 && !spec_allowed(c)) m.spec = 0;
     if (m.spec > 0) m.prod = 0;
-    // Period blocking (dependent row loads off the record chain of every
-    // exchange group) is chosen by the autotuner or PNS_BLOCKED.
-    m.block = 0;
+    // Period blocking takes the dependent row loads off the record chain of
+    // every exchange group (whose hottest replica sets the pace).
+    m.block = block_allowed(c) && cfg->warps_per_chain <= 1 ? 1 : 0;
     if (const char *e = getenv("PNS_BLOCKED")) m.block = atoi(e) && block_allowed(c) ? 1 : 0;
     if (m.block) {
         m.T = 1;

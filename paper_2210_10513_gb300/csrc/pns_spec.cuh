@@ -43,8 +43,8 @@ struct SpecSlot {
     int32_t j;       // bit to flip
     int32_t sat;     // multiplicity saturated
     int32_t dj;      // delta of bit j (int32 bits or float bits)
-    double m;        // multiplicity of a move
-    int64_t pad;
+    int32_t mi;      // multiplicity of a move (<= L0 < 2^31, an exact integer)
+    int32_t pad[3];
 };
 static_assert(sizeof(SpecSlot) == 32, "slot layout");
 
@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
             res.j = -1;
             res.sat = 0;
             res.dj = 0;
-            res.m = 0.0;
-            res.pad = 0;
+            res.mi = 0;
+            res.pad[0] = res.pad[1] = res.pad[2] = 0;
             const bool met = variant == VAR_METROPOLIS;
             const RecordDraws rd = record_draws(seed, chain_id, step, n, met, !met);
             if (variant == VAR_METROPOLIS) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 if (rd.mlu < y) {
                     res.move = 1;
                     res.j = rd.mi;
-                    res.m = 1.0;
+                    res.mi = 1;
                     if constexpr (std::is_same<D_t, float>::value) res.dj = __float_as_int(d);
                     else res.dj = d;
                 }
@@ -192,54 +192,76 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 }
                 const D_t amin = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin));
                 const float af = A::tof(amin);
-                const float anchor_f = af > 0.0f ? det_expf(-__fmul_rn(beta, af)) : 1.0f;
-                uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
-                auto visit = [&](int t, D_t dv, uint32_t word) {
-                    const float wt = det_expf(-__fmul_rn(beta, A::diff(A::pos(dv), amin)));
-                    const float ws = __fmul_rn(wt, 65536.0f);
+                const float anchor_e = det_expf(-__fmul_rn(beta, af));
+                const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
+                // Weights and their quantised sum first: the multiplicity
+                // alone decides a stay, and a stay needs no race winner, so
+                // the race (exponentials, divisions, argmin) runs only for a
+                // record that moves.  Its random numbers are counter-based,
+                // so the order of evaluation does not change them.
+                uint32_t sa = 0u, sb = 0u;
+                float wt[CPT];
+                auto weight = [&](D_t dv) -> float {
+                    const float wv = det_expf(-__fmul_rn(beta, A::diff(A::pos(dv), amin)));
+                    const float ws = __fmul_rn(wv, 65536.0f);
                     const float wa = truncf(ws);
                     sa += __float2uint_rz(wa);
                     sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                    const float ex = race_exp(word);
-                    const uint32_t kb = __float_as_uint(__fdiv_rn(ex, wt));
-                    if (kb < bkey) {
-                        bkey = kb;
-                        bpos = static_cast<uint32_t>(t);
-                    }
+                    return wv;
                 };
                 if (fast) {
-                    uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t0 >> 2));
-                    uint32_t cur_b = static_cast<uint32_t>(t0 >> 2);
 #pragma unroll
                     for (int u = 0; u < CPT; ++u) {
                         const int t = t0 + u;
-                        if (u < cpl && t < k) {
-                            const uint32_t bt = static_cast<uint32_t>(t) >> 2;
-                            if (bt != cur_b) {
-                                blk = rng_block(seed, TAG_RACE, chain_id, step, bt);
-                                cur_b = bt;
-                            }
-                            visit(t, dl[u], pick_word(blk, static_cast<uint32_t>(t) & 3u));
-                        }
+                        if (u < cpl && t < k) wt[u] = weight(dl[u]);
                     }
                 } else {
-                    for (int t = lane; t < k; t += 32)
-                        visit(t, delta_of(cand(t)), rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t)));
+                    for (int t = lane; t < k; t += 32) weight(delta_of(cand(t)));
                 }
-                const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
-                const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
                 const uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa);
                 const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
                 const uint64_t S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
                 const Mult mu = multiplicity_e1(S, k, anchor_f, rd.e1);
                 const bool fits = mu.mi >= 0 ? mu.mi <= Lw : mu.md <= static_cast<double>(Lw);
-                if (fits) {
+                if (fits) {  // (uniform across the warp)
+                    uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu;
+                    auto race = [&](int t, float wv, uint32_t word) {
+                        const uint32_t kb = __float_as_uint(__fdiv_rn(race_exp(word), wv));
+                        if (kb < bkey) {  // t ascending per lane: the first minimum is kept
+                            bkey = kb;
+                            bpos = static_cast<uint32_t>(t);
+                        }
+                    };
+                    if (fast) {
+                        uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t0 >> 2));
+                        uint32_t cur_b = static_cast<uint32_t>(t0 >> 2);
+#pragma unroll
+                        for (int u = 0; u < CPT; ++u) {
+                            const int t = t0 + u;
+                            if (u < cpl && t < k) {
+                                const uint32_t bt = static_cast<uint32_t>(t) >> 2;
+                                if (bt != cur_b) {
+                                    blk = rng_block(seed, TAG_RACE, chain_id, step, bt);
+                                    cur_b = bt;
+                                }
+                                race(t, wt[u], pick_word(blk, static_cast<uint32_t>(t) & 3u));
+                            }
+                        }
+                    } else {
+                        for (int t = lane; t < k; t += 32) {
+                            const D_t dv = delta_of(cand(t));
+                            const float wv = det_expf(-__fmul_rn(beta, A::diff(A::pos(dv), amin)));
+                            race(t, wv, rng_word(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t)));
+                        }
+                    }
+                    const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
+                    const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
                     const int j = cand(static_cast<int>(wpos));
                     const D_t dj = delta_of(j);
                     res.move = 1;
                     res.j = j;
                     res.sat = mu.sat;
-                    res.m = mu.md;
+                    res.mi = static_cast<int32_t>(mu.mi >= 0 ? mu.mi : static_cast<int64_t>(mu.md));
                     if constexpr (std::is_same<D_t, float>::value) res.dj = __float_as_int(dj);
                     else res.dj = dj;
                 }
@@ -249,12 +271,11 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
         sync_team();
         if (use_list && ctl[1]) dead = 1;
         // ---- commit: the records up to and including the first mover -------
-        int first = Dr;
-        for (int q = 0; q < Dr; ++q)
-            if (slots[q].move) {
-                first = q;
-                break;
-            }
+        uint32_t movers = 0u;  // (independent shared loads, no dependent scan)
+#pragma unroll
+        for (int q = 0; q < D; ++q)
+            if (q < Dr && slots[q].move) movers |= 1u << q;
+        const int first = movers ? __ffs(static_cast<int>(movers)) - 1 : Dr;
         const int ncommit = first < Dr ? first + 1 : Dr;
         if (P.tape == 2) {
             // every committed record starts from the current state
@@ -263,43 +284,39 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 if (tape_pos + q < P.tape_cap) {
                     const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos + q;
                     P.tape_x[o * P.W + wd] = wd < ld / 32 ? xw[wd] : 0u;
-                    if (wd == 0) P.tape_E[o] = st.E;
                 }
             }
+            if (tid == 0)  // (the energy is kept by thread 0)
+                for (int q = 0; q < ncommit && tape_pos + q < P.tape_cap; ++q)
+                    P.tape_E[static_cast<int64_t>(cid) * P.tape_cap + tape_pos + q] = st.E;
         }
         if (w < ncommit && lane == 0 && P.tape && tape_pos + w < P.tape_cap) {
             const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + tape_pos + w;
             const bool mv = w == first;
             const int64_t Lq = w == 0 ? st.L : P.L0;
             P.tape_flip[o] = mv ? slots[w].j : -1;
-            P.tape_m[o] = mv ? slots[w].m : (variant == VAR_METROPOLIS ? 1.0 : static_cast<double>(Lq));
+            P.tape_m[o] = static_cast<double>(mv ? static_cast<int64_t>(slots[w].mi) : (variant == VAR_METROPOLIS ? 1 : Lq));
         }
-        // budget / set bookkeeping of the committed records
-        for (int q = 0; q < ncommit; ++q) {
-            const int64_t Lq = q == 0 ? st.L : P.L0;
-            if (q == first) {
-                if (variant == VAR_UNBIASED) {
-                    const double mq = slots[q].m;
-                    const int64_t mi = static_cast<int64_t>(mq);
-                    st.L = Lq - mi;
-                    sum_int += mi;
-                } else {
-                    sum_int += 1;
-                }
-            } else {
-                if (variant == VAR_UNBIASED) {
-                    sum_int += Lq;
-                    st.L = P.L0;
-                    int ns = st.set_start + k;
-                    while (ns >= n) ns -= n;
-                    st.set_start = ns;
-                    st.period_start = static_cast<int64_t>(step0) + q + 1;
-                } else {
-                    sum_int += 1;
-                }
-                st.stays += 1;
+        // budget / set bookkeeping of the committed records, in closed form:
+        // records 0 .. nstay-1 stay (each a period end for Unbiased PNS:
+        // record (stay, L), L <- L0, next set), then the mover if any
+        const int nstay = first < Dr ? first : Dr;
+        if (variant == VAR_UNBIASED) {
+            if (nstay > 0) {
+                sum_int += st.L + static_cast<int64_t>(nstay - 1) * P.L0;
+                st.L = P.L0;
+                st.set_start = static_cast<int>((static_cast<int64_t>(st.set_start) + static_cast<int64_t>(nstay) * k) % n);
+                st.period_start = static_cast<int64_t>(step0) + nstay;
             }
+            if (first < Dr) {
+                const int64_t mi = slots[first].mi;
+                st.L -= mi;
+                sum_int += mi;
+            }
+        } else {
+            sum_int += ncommit;
         }
+        st.stays += nstay;
         if (use_list) {
             if (first < Dr) {
                 // the mover's set is the current one from now on
@@ -314,9 +331,6 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
             const SpecSlot mv = slots[first];
             if (mv.sat) st.saturated += 1;
             st.flips += 1;
-            double dE;
-            if constexpr (std::is_same<D_t, float>::value) dE = static_cast<double>(__int_as_float(mv.dj));
-            else dE = static_cast<double>(mv.dj);
             // all warps apply the row
             const int j = mv.j;
             const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
@@ -336,9 +350,15 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
             }
             for (; c < chunks; c += TT) add_chunk<QT, HT>(h + c * VE, ld_nc_v4(row + c * VE), up);
             sync_team();
-            if (tid == 0) xw[j >> 5] ^= 1u << (j & 31);
-            st.E = __dadd_rn(st.E, dE);
-            st.best_E = fmin(st.best_E, st.E);
+            if (tid == 0) {
+                xw[j >> 5] ^= 1u << (j & 31);
+                // the fp64 energy lives in thread 0 only (GB300's fp64 pipe is narrow)
+                double dE;
+                if constexpr (std::is_same<D_t, float>::value) dE = static_cast<double>(__int_as_float(mv.dj));
+                else dE = static_cast<double>(mv.dj);
+                st.E = __dadd_rn(st.E, dE);
+                st.best_E = fmin(st.best_E, st.E);
+            }
         }
         st.step += ncommit;
         tape_pos += ncommit;

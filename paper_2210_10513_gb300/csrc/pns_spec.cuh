@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                     lst = lb;
                 } else {
                     // start advances by k per skipped period
-                    int64_t s64 = static_cast<int64_t>(st.set_start) + static_cast<int64_t>(w) * k;
-                    start = static_cast<int>(s64 % n);
+                    // (32-bit: set_start < n, w < D <= 16, k <= 128)
+                    start = static_cast<int>(static_cast<uint32_t>(st.set_start + w * k) % static_cast<uint32_t>(n));
                 }
                 auto cand = [&](int t) -> int {
                     if (lst) return lst[t];
@@ -305,7 +305,9 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
             if (nstay > 0) {
                 sum_int += st.L + static_cast<int64_t>(nstay - 1) * P.L0;
                 st.L = P.L0;
-                st.set_start = static_cast<int>((static_cast<int64_t>(st.set_start) + static_cast<int64_t>(nstay) * k) % n);
+                // (set_start < n, nstay <= D <= 16, k <= 128: 32-bit arithmetic)
+                st.set_start = static_cast<int>(static_cast<uint32_t>(st.set_start + nstay * k) %
+                                                static_cast<uint32_t>(n));
                 st.period_start = static_cast<int64_t>(step0) + nstay;
             }
             if (first < Dr) {

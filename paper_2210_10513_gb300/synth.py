@@ -40,6 +40,16 @@ def dense_normal(n, sigma, seed, stream=0):
     return ((a + a.T) * np.float32(0.5)).astype(np.float32)
 
 
+def upper_triangular_qubo(n, sigma, seed, stream=2):
+    """The paper's random QUBO instance (Sec. 4): U_ij ~ N(0, sigma^2) for
+    i <= j, target exp(x^T U x).  Returned in this library's convention,
+    E(x) = x^T Q x with pi ~ exp(-beta E): Q = -(U + U^T) / 2 (fp32; halving
+    and negating are exact)."""
+    g = _rng(seed, stream)
+    u = np.triu(g.standard_normal(size=(n, n)) * sigma).astype(np.float32)
+    return (-(u + u.T) * np.float32(0.5)).astype(np.float32)
+
+
 def vector_normal(n, sigma, seed, stream=1):
     g = _rng(seed, stream)
     return (g.standard_normal(size=n) * sigma).astype(np.float32)

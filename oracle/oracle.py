@@ -56,7 +56,7 @@ def lib():
         L.oq_decide.restype = i32
         L.oq_random_subset.argtypes = [i32, i32, u64, u32, u64, vp]
         L.oq_random_subset.restype = i32
-        L.oq_run_chain.argtypes = [vp, vp, f32, u32, vp, vp, vp, vp, i64, i64, vp, vp, vp]
+        L.oq_run_chain.argtypes = [vp, vp, f32, u32, vp, vp, vp, vp, i64, i64, vp, vp, vp, vp]
         L.oq_run_chain.restype = i32
         L.oq_swap_round.argtypes = [i32, vp, vp, vp, u64, u32, u64, vp]
         L.oq_swap_round.restype = i32
@@ -147,6 +147,7 @@ class ChainState:
         self.st.E = E
         self.st.best_E = E
         self.st.beta_idx = beta_idx
+        self.x_best = self.x.copy()  # X_max of Algorithms 8-10
 
 
 def make_config(variant, k=0, subset="systematic", L0=100, seed=0):
@@ -170,7 +171,7 @@ def run_chain(problem, cfg, beta, chain_id, state, n_records, stop_after_periods
     hf = state.h if problem.is_float else None
     rc = lib().oq_run_chain(C.byref(problem.struct), C.byref(cfg), C.c_float(beta), chain_id,
                             _ptr(state.x), _ptr(hi), _ptr(hf), C.byref(state.st), int(n_records),
-                            int(stop_after_periods), _ptr(flips), _ptr(ms), C.byref(got))
+                            int(stop_after_periods), _ptr(flips), _ptr(ms), C.byref(got), _ptr(state.x_best))
     if rc != 0:
         raise RuntimeError("oracle run_chain failed with code %d" % rc)
     r = got.value
@@ -296,7 +297,8 @@ def run_independent(problems, betas, cfg_kwargs, chains_per_replica, x0, n_recor
         stt = ChainState(prob, bits, cfg.L0, beta_idx=r)
         beta = float(np.float32(betas[p][r]))
         fl, ms = run_chain(prob, cfg, beta, cid, stt, n_records, tape=tape)
-        out[cid] = dict(flips=fl, m=ms, x=stt.x.copy(), h=stt.h.copy(), state=stt.st, instance=p, group=gid)
+        out[cid] = dict(flips=fl, m=ms, x=stt.x.copy(), h=stt.h.copy(), state=stt.st, instance=p, group=gid,
+                        x_best=stt.x_best.copy())
     return out
 
 

@@ -461,8 +461,12 @@ int oq_random_subset(int32_t n, int32_t k, uint64_t seed, uint32_t chain, uint64
 int oq_run_chain(const oq_problem *P, const oq_config *C, float beta, uint32_t chain,
                  uint8_t *x, int64_t *h_i, float *h_f, oq_chain *S,
                  int64_t max_records, int64_t stop_after_periods,
-                 int32_t *tape_flip, double *tape_m, int64_t *records_out)
+                 int32_t *tape_flip, double *tape_m, int64_t *records_out, uint8_t *x_best)
 {
+    /* x_best (may be NULL): X_max of Algorithms 8-10, the state of lowest
+     * energy seen so far (highest pi at any beta > 0); it changes only on a
+     * strict improvement, so it stays the initial state until E drops below
+     * the initial energy. */
     int n = P->n;
     int k;
     switch (C->variant) {
@@ -552,7 +556,10 @@ int oq_run_chain(const oq_problem *P, const oq_config *C, float beta, uint32_t c
         if (tape_flip) tape_flip[rec] = flip;
         if (tape_m) tape_m[rec] = m;
         S->sum_m = S->sum_m + m;
-        if (S->E < S->best_E) S->best_E = S->E;
+        if (S->E < S->best_E) {
+            S->best_E = S->E;
+            if (x_best) memcpy(x_best, x, (size_t)n);
+        }
         S->step += 1;
         rec += 1;
     }

@@ -339,3 +339,26 @@ def test_random_subset_uniform_and_distinct():
     exp = 30000 / math.comb(n, k)
     chi2 = ((c - exp) ** 2 / exp).sum()
     assert chi2 < 180  # 119 dof, p ~ 3e-4
+
+
+@pytest.mark.parametrize("variant,k", [("basic", 3), ("rf", 0), ("unbiased", 4)])
+def test_best_state_is_first_minimum_of_the_replayed_path(variant, k):
+    """X_max of Algorithms 8-10: replaying the flip tape from x0 and
+    enumerating the energies of the visited states, the oracle's best state
+    is the first state of lowest energy on the path (updates only on strict
+    improvement) and best_E is that energy."""
+    n = 12
+    q = synth.dense_int(n, -9, 9, 21, np.int32)
+    b = synth.vector_int(n, -9, 9, 21, np.int32)
+    prob = O.Problem(q=q, b=b)
+    x0 = synth.random_bits(1, n, seed=4)[0]
+    cfg = O.make_config(variant, k=k, L0=20, seed=7)
+    st = O.ChainState(prob, x0, 20)
+    flips, _ = O.run_chain(prob, cfg, np.float32(0.3), 3, st, 3000)
+    E_all = X.energies(q.astype(np.float64), b.astype(np.float64))
+    before, last = X.replay_codes(X.code_of(x0), flips)
+    path = np.concatenate([before, [last]])  # the start, then the state after each record
+    e_path = E_all[path]
+    first_min = int(np.argmin(e_path))  # argmin returns the first occurrence
+    assert st.st.best_E == e_path[first_min]
+    assert X.code_of(st.x_best) == int(path[first_min])

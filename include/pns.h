@@ -118,6 +118,11 @@ typedef struct {
                                   per CTA) on short probe runs and keeps the fastest; results
                                   do not depend on the mapping.  Choices are cached in the file
                                   named by PNS_AUTOTUNE_CACHE when that variable is set. */
+    int32_t track_best;        /* 1: keep each chain's lowest-energy state X_max, the output of the
+                                  optimisation forms (Algorithms 8-10: with variant BASIC this is
+                                  Optimization PNS, with RF Optimization Rejection-Free, at the
+                                  constant temperature 1/beta); read it with pns_read_best.  Runs
+                                  on the per-flip kernel. */
     int32_t reserved;          /* must be 0 */
 } pns_config;
 
@@ -189,6 +194,13 @@ pns_status pns_read(pns_ctx *ctx, uint32_t *states, double *multiplicities, int3
  * at the start of each record, i.e. the jump-chain state J that the record's
  * multiplicity M weighs (Sec. 1.2, Theorem 3 (5)). */
 pns_status pns_read_samples(pns_ctx *ctx, uint32_t *states, double *energies, void *stream);
+
+/* With cfg.track_best = 1, copies every chain's X_max (Algorithms 8-10): the
+ * state of lowest energy the chain has visited, which changes only when the
+ * energy drops strictly below the best so far and so starts as the initial
+ * state; chains x W words, host or device memory.  Its energy is
+ * pns_stats.best_energy.  Synchronises `stream`. */
+pns_status pns_read_best(pns_ctx *ctx, uint32_t *states, void *stream);
 
 /* Scalars of a multiplicity-weighted sample: weight W = sum M, <E>, Var(E),
  * number of samples. */

@@ -86,6 +86,7 @@ struct pns_ctx {
     double *d_tape_m = nullptr;
     uint32_t *d_tape_x = nullptr;   // tape = 2
     double *d_tape_E = nullptr;
+    uint32_t *d_xbest = nullptr;    // track_best: X_max per chain (W words)
     int64_t tape_alloc = 0;  // records per chain allocated
     int64_t tape_cap = 0;    // records per chain of the last run
     // plan
@@ -109,7 +110,7 @@ void free_ctx(pns_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void *ptrs[] = {c->d_q, c->d_rowptr, c->d_col, c->d_diag, c->d_b, c->d_betas, c->d_inst, c->d_chain,
                     c->d_state, c->d_x, c->d_fields, c->d_cta, c->d_cta_chains, c->d_status, c->d_tape_flip,
-                    c->d_tape_m,  c->d_tape_x, c->d_tape_E};
+                    c->d_tape_m,  c->d_tape_x, c->d_tape_E, c->d_xbest};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -131,6 +132,7 @@ pns_status check_args(const pns_problem *probs, int32_t n_probs, const pns_confi
     if (cfg->swap_interval < 0) return fail(PNS_ERR_INVALID_ARG, "swap_interval must be >= 0");
     if (cfg->graph != 0 && cfg->graph != 1) return fail(PNS_ERR_INVALID_ARG, "graph must be 0 or 1");
     if (cfg->autotune != 0 && cfg->autotune != 1) return fail(PNS_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (cfg->track_best != 0 && cfg->track_best != 1) return fail(PNS_ERR_INVALID_ARG, "track_best must be 0 or 1");
     if (cfg->chains_per_cta < 0 || cfg->reserved != 0 || cfg->chain_base < 0 || cfg->group_base < 0)
         return fail(PNS_ERR_INVALID_ARG, "chains_per_cta, chain_base, group_base must be >= 0 and reserved 0");
     if (cfg->swap_interval > 0) {
@@ -421,11 +423,12 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
         m.spec = (d == 0 || spec_supported(c.qtype, d)) ? d : 0;
     }
     if (m.spec > 0 && !spec_allowed(c)) m.spec = 0;
+    if (cfg->track_best) m.spec = 0;  // X_max is kept by the per-flip kernel
     if (m.spec > 0) m.prod = 0;
     // Period blocking takes the dependent row loads off the record chain of
     // every exchange group (whose hottest replica sets the pace).
-    m.block = block_allowed(c) && cfg->warps_per_chain <= 1 ? 1 : 0;
-    if (const char *e = getenv("PNS_BLOCKED")) m.block = atoi(e) && block_allowed(c) ? 1 : 0;
+    m.block = block_allowed(c) && cfg->warps_per_chain <= 1 && !cfg->track_best ? 1 : 0;
+    if (const char *e = getenv("PNS_BLOCKED")) m.block = atoi(e) && block_allowed(c) && !cfg->track_best ? 1 : 0;
     if (m.block) {
         m.T = 1;
         m.prod = 0;
@@ -555,6 +558,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         if (!sampler_supported(c->fmt, c->qtype, c->hbytes, m.T)) return;
         if (m.spec > 0 && (!spec_allowed(*c) || !spec_supported(c->qtype, m.spec))) return;
         if (m.block && (!block_allowed(*c) || m.T != 1)) return;
+        if (c->cfg.track_best && (m.block || m.spec > 0)) return;
         for (const Mapping &o : cands)
             if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta && o.block == m.block &&
                 o.gw == m.gw)
@@ -914,6 +918,11 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     CU(cudaMemcpyAsync(c->d_state, cs.data(), sizeof(ChainState) * cs.size(), cudaMemcpyHostToDevice, s));
     CU(launch_init_fields(c->fmt, c->qtype, c->hbytes, c->d_inst, c->d_chain, c->d_x, c->d_fields, c->d_state,
                           c->chains, c->W, c->LD, c->max_ld, s));
+    if (cfg->track_best) {
+        // X_max starts as the initial state (Algorithms 8-10)
+        CU(cudaMalloc(&c->d_xbest, sizeof(uint32_t) * c->W * c->chains));
+        CU(cudaMemcpyAsync(c->d_xbest, c->d_x, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDeviceToDevice, s));
+    }
     CU(cudaStreamSynchronize(s));
     if (cfg->autotune) {
         st = autotune(c, s);
@@ -979,6 +988,7 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.tape_m = c->d_tape_m;
     P.tape_x = c->d_tape_x;
     P.tape_E = c->d_tape_E;
+    P.xbest = c->tape_off ? nullptr : c->d_xbest;  // (autotuner probes leave X_max alone)
     P.status = c->d_status;
     P.tape_cap = c->tape_cap;
     P.steps = steps;
@@ -1109,6 +1119,17 @@ pns_status pns_read_samples(pns_ctx *c, uint32_t *states, double *energies, void
     return PNS_OK;
 }
 
+pns_status pns_read_best(pns_ctx *c, uint32_t *states, void *stream) {
+    if (!c || !states) return fail(PNS_ERR_INVALID_ARG, "NULL argument");
+    if (!c->d_xbest) return fail(PNS_ERR_STATE, "the context keeps no best states (needs track_best = 1)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pns_status st = sync_and_check(c, s);
+    if (st != PNS_OK) return st;
+    CU(cudaMemcpyAsync(states, c->d_xbest, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    return PNS_OK;
+}
+
 pns_status pns_moments(pns_ctx *c, int32_t instance, int32_t beta_idx, pns_moment_scalars *scalars, double *mean_x,
                        double *mean_xx, double *cov_ex, double *cov_exx, void *stream) {
     if (!c) return fail(PNS_ERR_INVALID_ARG, "ctx is NULL");
@@ -1191,8 +1212,9 @@ struct CkptHeader {
 
 pns_status pns_checkpoint(pns_ctx *c, void *buf, size_t *bytes) {
     if (!c || !bytes) return fail(PNS_ERR_INVALID_ARG, "NULL argument");
+    const size_t xb_bytes = c->d_xbest ? sizeof(uint32_t) * c->W * c->chains : 0;
     const size_t nbytes = sizeof(CkptHeader) + sizeof(ChainState) * c->chains + sizeof(uint32_t) * c->W * c->chains +
-                          static_cast<size_t>(c->hbytes) * c->LD * c->chains;
+                          static_cast<size_t>(c->hbytes) * c->LD * c->chains + xb_bytes;
     if (!buf) {
         *bytes = nbytes;
         return PNS_OK;
@@ -1210,6 +1232,8 @@ pns_status pns_checkpoint(pns_ctx *c, void *buf, size_t *bytes) {
     CU(cudaMemcpy(p, c->d_x, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDefault));
     p += sizeof(uint32_t) * c->W * c->chains;
     CU(cudaMemcpy(p, c->d_fields, static_cast<size_t>(c->hbytes) * c->LD * c->chains, cudaMemcpyDefault));
+    p += static_cast<size_t>(c->hbytes) * c->LD * c->chains;
+    if (xb_bytes) CU(cudaMemcpy(p, c->d_xbest, xb_bytes, cudaMemcpyDefault));
     *bytes = nbytes;
     return PNS_OK;
 }
@@ -1219,8 +1243,9 @@ pns_status pns_restore(pns_ctx *c, const void *buf, size_t bytes) {
     CkptHeader h;
     if (bytes < sizeof(h)) return fail(PNS_ERR_INVALID_ARG, "checkpoint too short");
     memcpy(&h, buf, sizeof(h));
+    const size_t xb_bytes = c->d_xbest ? sizeof(uint32_t) * c->W * c->chains : 0;
     const size_t nbytes = sizeof(CkptHeader) + sizeof(ChainState) * c->chains + sizeof(uint32_t) * c->W * c->chains +
-                          static_cast<size_t>(c->hbytes) * c->LD * c->chains;
+                          static_cast<size_t>(c->hbytes) * c->LD * c->chains + xb_bytes;
     if (h.magic != kCkptMagic || h.chains != c->chains || h.W != c->W || h.LD != c->LD || h.hbytes != c->hbytes ||
         h.fmt != c->fmt || bytes != nbytes)
         return fail(PNS_ERR_INVALID_ARG, "checkpoint does not match this context");
@@ -1231,6 +1256,8 @@ pns_status pns_restore(pns_ctx *c, const void *buf, size_t bytes) {
     CU(cudaMemcpy(c->d_x, p, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDefault));
     p += sizeof(uint32_t) * c->W * c->chains;
     CU(cudaMemcpy(c->d_fields, p, static_cast<size_t>(c->hbytes) * c->LD * c->chains, cudaMemcpyDefault));
+    p += static_cast<size_t>(c->hbytes) * c->LD * c->chains;
+    if (xb_bytes) CU(cudaMemcpy(c->d_xbest, p, xb_bytes, cudaMemcpyDefault));
     CU(cudaMemset(c->d_status, 0, sizeof(int32_t)));
     c->latched = 0;
     return PNS_OK;

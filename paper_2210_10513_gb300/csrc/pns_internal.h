@@ -73,6 +73,7 @@ struct KParams {
     double *tape_m;
     uint32_t *tape_x;       // tape = 2: state bits at each record's start, W words per record
     double *tape_E;         // tape = 2: energy at each record's start
+    uint32_t *xbest;        // NULL, or each chain's lowest-energy state (W words; X_max of Algorithms 8-10)
     int32_t *status;        // device status word (first error wins)
     int64_t tape_cap;
     int64_t steps;          // records (no exchange) or original samples (exchange)

@@ -687,9 +687,16 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                 write_record(-1, m);
             }
         }
-        st.best_E = fmin(st.best_E, st.E);
+        const bool improved = st.E < st.best_E;  // (the same for every thread of the team)
+        if (improved) st.best_E = st.E;
         st.step += 1;
         sync_cons();
+        if (improved && P.xbest) {
+            // X_max (Algorithms 8-10): the state after this record; the next
+            // change of the bits comes after a team barrier
+            uint32_t *xb = P.xbest + static_cast<int64_t>(cid) * P.W;
+            for (int q = ctid; q < P.W; q += TCC) xb[q] = q < ld / 32 ? xw[q] : 0u;
+        }
         return period_end;
     };
 

@@ -42,7 +42,7 @@ class pns_config(C.Structure):
                 ("L0", C.c_int64), ("swap_interval", C.c_int64), ("seed", C.c_uint64), ("tape", C.c_int32),
                 ("warps_per_chain", C.c_int32), ("chains_per_cta", C.c_int32), ("chain_base", C.c_int32),
                 ("x0", C.c_void_p), ("group_base", C.c_int32), ("graph", C.c_int32), ("autotune", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("track_best", C.c_int32), ("reserved", C.c_int32)]
 
 
 class pns_info(C.Structure):
@@ -72,7 +72,7 @@ assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
 
 EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_read_samples", "pns_moments",
            "pns_energy_grads", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore", "pns_destroy",
-           "pns_last_error", "pns_sample_static")
+           "pns_last_error", "pns_sample_static", "pns_read_best")
 STATIC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
@@ -103,6 +103,8 @@ def lib():
         L.pns_energy_grads.restype = C.c_int
         L.pns_sample_static.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, vp]
         L.pns_sample_static.restype = C.c_int
+        L.pns_read_best.argtypes = [vp, vp, vp]
+        L.pns_read_best.restype = C.c_int
         L.pns_destroy.argtypes = [vp]
         L.pns_destroy.restype = None
         L.pns_last_error.argtypes = []
@@ -197,7 +199,7 @@ def make_problem(n, q=None, b=None, betas=(1.0,), csr=None, k=0, keep=None):
 
 def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100, swap_interval=0, seed=0,
                 tape=False, warps_per_chain=0, x0=None, chains_per_cta=0, chain_base=0, group_base=0, graph=False,
-                autotune=False):
+                autotune=False, track_best=False):
     c = pns_config()
     c.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     c.k = int(k)
@@ -213,6 +215,7 @@ def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica
     c.group_base = int(group_base)
     c.graph = int(bool(graph))
     c.autotune = int(bool(autotune))
+    c.track_best = int(bool(track_best))
     c.x0 = _addr(x0)
     return c
 
@@ -244,6 +247,10 @@ def pns_read(ctx, states=None, multiplicities=None, flips=None, stats=None, stre
 
 def pns_read_samples(ctx, states=None, energies=None, stream=None):
     _check(lib().pns_read_samples(ctx, _addr(states), _addr(energies), _stream(stream)))
+
+
+def pns_read_best(ctx, states, stream=None):
+    _check(lib().pns_read_best(ctx, _addr(states), _stream(stream)))
 
 
 def pns_moments(ctx, instance, beta_idx, scalars=None, mean_x=None, mean_xx=None, cov_ex=None, cov_exx=None,
@@ -295,7 +302,7 @@ class Sampler:
 
     def __init__(self, problems, variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100,
                  swap_interval=0, seed=0, tape=False, warps_per_chain=0, x0=None, stream=None, chains_per_cta=0,
-                 chain_base=0, group_base=0, graph=False, autotune=False):
+                 chain_base=0, group_base=0, graph=False, autotune=False, track_best=False):
         keep = []
         probs = []
         for pr in problems:
@@ -303,7 +310,7 @@ class Sampler:
         if x0 is not None:
             keep.append(x0)
         cfg = make_config(variant, k, subset, chains_per_replica, L0, swap_interval, seed, tape, warps_per_chain, x0,
-                          chains_per_cta, chain_base, group_base, graph, autotune)
+                          chains_per_cta, chain_base, group_base, graph, autotune, track_best)
         self.ctx = pns_create(probs, cfg, stream)
         self.info = pns_get_info(self.ctx)
         self.tape = bool(tape)
@@ -333,6 +340,13 @@ class Sampler:
         e = np.empty((info.chains, info.tape_capacity), dtype=np.float64)
         pns_read_samples(self.ctx, x, e, stream)
         return x, e
+
+    def best(self, stream=None):
+        """X_max of every chain (chains x W words, track_best = 1)."""
+        info = pns_get_info(self.ctx)
+        out = np.empty((info.chains, info.words_per_chain), dtype=np.uint32)
+        pns_read_best(self.ctx, out, stream)
+        return out
 
     def moments(self, n, instance=0, beta_idx=0, stream=None, device=None):
         """Multiplicity-weighted moments (fp64): scalars [W, <E>, Var E, samples],

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) ex[u] = exn[u];
             e1 = e1n;
-            double m = mu.md;
+            double m = mult_md(mu);
             const D dj = delta_t(a, j);
             __syncwarp();
             bool period_end = false;

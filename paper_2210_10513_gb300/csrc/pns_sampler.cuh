@@ -143,10 +143,25 @@ __device__ __forceinline__ RecordDraws record_draws(uint64_t seed, uint32_t chai
 // critical path, and as the fp64 record value.  GB300's fp64 pipe has a
 // 64-cycle latency, so nothing on the per-record chain waits for the double.
 struct Mult {
-    int64_t mi;    // M when small (-1: large, use md)
-    double md;     // M as recorded
+    int64_t mi;    // M when M < 2^24 + 1 (else -1)
+    float fgl;     // large M: floor(g) = M - 1 (an integer in fp32); +inf when saturated
     int sat;
 };
+
+// M as recorded (fp64), formed only where it is needed (tape, sums): the
+// fp64 pipe is narrow on GB300, so the decision path avoids it.
+__device__ __forceinline__ double mult_md(const Mult &mu) {
+    if (mu.mi >= 0) return static_cast<double>(static_cast<int32_t>(mu.mi));
+    if (mu.sat) return 9223372036854775808.0;
+    return __dadd_rn(static_cast<double>(mu.fgl), 1.0);
+}
+
+// M <= L for a budget L >= 0, compared as the fp64 record value (as the
+// specification does); fp64 is touched only in the rare large-M branch.
+__device__ __forceinline__ bool mult_fits(const Mult &mu, int64_t L) {
+    if (mu.mi >= 0) return mu.mi <= L;
+    return mult_md(mu) <= static_cast<double>(L);
+}
 
 // Round-to-nearest-even conversion of an unsigned 64-bit integer to fp32 with
 // 32-bit integer operations only (GB300 runs 64-bit int<->float conversions on
@@ -184,31 +199,30 @@ __device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anc
     ps = __fdiv_rn(ps, __int2float_rn(k));
     const float p = __fmul_rn(ps, anchor_f);
     r.sat = 0;
+    r.fgl = 0.0f;
     if (p >= 1.0f) {
         r.mi = 1;
-        r.md = 1.0;
         return r;
     }
     if (p <= 0.0f) {
         r.sat = 1;
         r.mi = -1;
-        r.md = 9223372036854775808.0;
+        r.fgl = __int_as_float(0x7f800000);
         return r;
     }
     const float g = __fdiv_rn(e1, det_neg_log1m(p));
     if (!(g < 0x1p63f)) {
         r.sat = 1;
         r.mi = -1;
-        r.md = 9223372036854775808.0;
+        r.fgl = __int_as_float(0x7f800000);
         return r;
     }
     const float fg = floorf(g);
     if (fg < 16777216.0f) {
         r.mi = static_cast<int64_t>(__float2int_rz(fg)) + 1;
-        r.md = static_cast<double>(static_cast<int32_t>(r.mi));
     } else {
         r.mi = -1;
-        r.md = __dadd_rn(static_cast<double>(fg), 1.0);
+        r.fgl = fg;
     }
     return r;
 }
@@ -655,7 +669,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             if (always_move) prefetch_row(j);
             // a5: multiplicity and budget
             const Mult mu = multiplicity_e1(S, k, anchor_f, rd.e1);
-            double m = mu.md;
+            double m = mult_md(mu);
             const int sat = mu.sat;
             const D dj = delta_of(j);
             sync_cons();  // reads of h, x and the list are done

@@ -156,6 +156,14 @@ __device__ __forceinline__ double mult_md(const Mult &mu) {
     return __dadd_rn(static_cast<double>(mu.fgl), 1.0);
 }
 
+// M <= L for a budget 0 <= L < 2^31, in 32-bit arithmetic: every M that can
+// fit is then below 2^31 and exact in fp32's integer range used here, so the
+// result equals the fp64 comparison of mult_fits.
+__device__ __forceinline__ bool mult_fits_small(const Mult &mu, int32_t L) {
+    if (mu.mi >= 0) return mu.mi <= L;
+    return !mu.sat && mu.fgl < 2147483648.0f && __float2int_rz(mu.fgl) < L;
+}
+
 // M <= L for a budget L >= 0, compared as the fp64 record value (as the
 // specification does); fp64 is touched only in the rare large-M branch.
 __device__ __forceinline__ bool mult_fits(const Mult &mu, int64_t L) {

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
                 const uint64_t S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
                 const Mult mu = multiplicity_e1(S, k, anchor_f, rd.e1);
-                const bool fits = mult_fits(mu, Lw);
+                const bool fits = mult_fits_small(mu, static_cast<int32_t>(Lw));  // (L0 < 2^31 here)
                 if (fits) {  // (uniform across the warp)
                     uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu;
                     auto race = [&](int t, float wv, uint32_t word) {

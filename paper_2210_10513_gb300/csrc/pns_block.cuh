@@ -364,9 +364,9 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
             const D dj = delta_t(a, j);
             __syncwarp();
             bool period_end = false;
-            const bool fits = mu.mi >= 0 ? mu.mi <= st.L : m <= static_cast<double>(st.L);
+            const bool fits = mult_fits_small(mu, static_cast<int32_t>(st.L));  // (L0 < 2^31 here)
             if (fits) {
-                st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(m);
+                st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(__float2int_rz(mu.fgl)) + 1;
                 if (mu.sat) st.saturated += 1;
                 const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
                 if (lane == 0) prefetch_l2(Q + static_cast<int64_t>(j) * ld, row_bytes);

@@ -380,7 +380,7 @@ static bool block_allowed(const pns_ctx &c) {
     int kmax = 1;
     for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
     return c.fmt == PNS_DENSE && c.cfg.swap_interval > 0 && c.cfg.variant == PNS_UNBIASED && c.R <= 16 &&
-           c.cfg.subset == PNS_SUBSET_SYSTEMATIC && block_supported(c.qtype, kmax);
+           c.cfg.L0 < (1ll << 31) && c.cfg.subset == PNS_SUBSET_SYSTEMATIC && block_supported(c.qtype, kmax);
 }
 
 static bool spec_allowed(const pns_ctx &c) {

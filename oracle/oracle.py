@@ -63,6 +63,12 @@ def lib():
         L.oq_run_alg11.argtypes = [vp, i32, i64, f32, u64, u32, vp, vp, vp, i64, vp]
         L.oq_run_alg11.restype = i32
         L.oq_philox.argtypes = [vp, u32, u32, vp]
+        L.oq_donuts_chain.argtypes = [vp, u32, i64, f32, f32, vp]
+        L.oq_donuts_chain.restype = i32
+        L.oq_sincos2pi_vec.argtypes = [vp, vp, vp, i64]
+        L.oq_normal_pair_vec.argtypes = [vp, vp, vp, vp, i64]
+        L.oq_donut_energy.argtypes = [f32, f32, f32, f32]
+        L.oq_donut_energy.restype = f32
         L.oq_rng_word.argtypes = [u64, u32, u32, u64, u32]
         L.oq_rng_word.restype = u32
         for name in ("oq_logf_vec", "oq_expf_vec", "oq_neg_log1m_vec", "oq_uniform_fine32_vec",
@@ -334,3 +340,54 @@ def run_tempering(problem, betas, cfg_kwargs, group_id, chain_id0, x0s, rounds, 
         ms = np.concatenate(tapes[s][1]) if tape else None
         res.append(dict(flips=fl, m=ms, x=states[s].x.copy(), h=states[s].h.copy(), state=states[s].st))
     return res
+
+
+# ---------------------------------------------------------------------------
+# Continuous Unbiased PNS (Algorithm 7) and Metropolis on the Donuts target
+# (Sec. 7).
+# ---------------------------------------------------------------------------
+class _DonutsCfg(C.Structure):
+    _fields_ = [("mu0", C.c_float), ("c", C.c_float), ("L0", C.c_int64), ("seed", C.c_uint64),
+                ("variant", C.c_int32), ("npairs", C.c_int32)]
+
+
+class _DonutsStats(C.Structure):
+    _fields_ = [("weight", C.c_double), ("sum_x", C.c_double * 2), ("sum_x2", C.c_double * 2),
+                ("sum_x4", C.c_double * 2), ("sum_pos", C.c_double * 2), ("records", C.c_int64),
+                ("moves", C.c_int64), ("budget_left", C.c_int64), ("period_start", C.c_int64),
+                ("x", C.c_float * 2)]
+
+
+def donuts_chain(variant, chain, steps, x0, mu0=9.0, c=50.0, L0=1000, seed=0, npairs=25):
+    """One oracle chain on the Donuts target; returns its statistics as a dict
+    (weight, sum_x, sum_x2, sum_x4, sum_pos as 2-arrays, records, moves,
+    budget_left, period_start, x)."""
+    cfg = _DonutsCfg(np.float32(mu0), np.float32(c), int(L0), int(seed) & (2**64 - 1), VARIANTS[variant], int(npairs))
+    st = _DonutsStats()
+    rc = lib().oq_donuts_chain(C.byref(cfg), int(chain), int(steps), C.c_float(x0[0]), C.c_float(x0[1]), C.byref(st))
+    if rc:
+        raise RuntimeError("oq_donuts_chain failed with code %d" % rc)
+    return dict(weight=st.weight, sum_x=np.array(st.sum_x[:]), sum_x2=np.array(st.sum_x2[:]),
+                sum_x4=np.array(st.sum_x4[:]), sum_pos=np.array(st.sum_pos[:]), records=st.records, moves=st.moves,
+                budget_left=st.budget_left, period_start=st.period_start, x=np.array(st.x[:], dtype=np.float32))
+
+
+def sincos2pi(u):
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    c = np.empty_like(u)
+    s = np.empty_like(u)
+    lib().oq_sincos2pi_vec(_ptr(u), _ptr(c), _ptr(s), u.size)
+    return c, s
+
+
+def normal_pairs(w0, w1):
+    w0 = np.ascontiguousarray(w0, dtype=np.uint32)
+    w1 = np.ascontiguousarray(w1, dtype=np.uint32)
+    z1 = np.empty(w0.shape, np.float32)
+    z2 = np.empty(w0.shape, np.float32)
+    lib().oq_normal_pair_vec(_ptr(w0), _ptr(w1), _ptr(z1), _ptr(z2), w0.size)
+    return z1, z2
+
+
+def donut_energy(x1, x2, mu0=9.0, c=50.0):
+    return lib().oq_donut_energy(np.float32(mu0), np.float32(c), np.float32(x1), np.float32(x2))

@@ -635,6 +635,178 @@ int oq_run_alg11(const oq_problem *P, int32_t k, int64_t L0, float beta, uint64_
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Continuous Unbiased PNS (Algorithm 7) and Metropolis on the Donuts target */
+/* (Sec. 7): f(x) ~ exp[-(x1^2 + x2^2 - mu0)^2 / (2 sigma^2)], written as    */
+/* exp(-E(x)) with E(x) = c (x1^2 + x2^2 - mu0)^2, c = 1 / (2 sigma^2).      */
+/* ------------------------------------------------------------------------ */
+
+/* (cos 2 pi u, sin 2 pi u) for u in [0, 1): quadrant q = floor(4u), angle
+ * theta = (4u - q) pi / 2 in [0, pi / 2), Taylor series of sin to theta^11
+ * and of cos to theta^12 (Horner in theta^2), then the quadrant's rotation. */
+void oq_sincos2pi(float u, float *c_out, float *s_out)
+{
+    float u4 = u * 4.0f;                  /* exact */
+    float qf = floorf(u4);
+    float f = u4 - qf;                    /* exact */
+    int q = (int)qf;
+    float t = f * 0x1.921fb6p+0f;         /* pi / 2 */
+    float t2 = t * t;
+    float ps = -0x1.ae6456p-26f;          /* -1/11! */
+    ps = 0x1.71de3ap-19f + t2 * ps;       /* 1/9! */
+    ps = -0x1.a01a02p-13f + t2 * ps;      /* -1/7! */
+    ps = 0x1.111112p-7f + t2 * ps;        /* 1/5! */
+    ps = -0x1.555556p-3f + t2 * ps;       /* -1/3! */
+    float sn = t + t * (t2 * ps);
+    float pc = 0x1.1eed8ep-29f;           /* 1/12! */
+    pc = -0x1.27e4fcp-22f + t2 * pc;      /* -1/10! */
+    pc = 0x1.a01a02p-16f + t2 * pc;       /* 1/8! */
+    pc = -0x1.6c16c2p-10f + t2 * pc;      /* -1/6! */
+    pc = 0x1.555556p-5f + t2 * pc;        /* 1/4! */
+    pc = -0.5f + t2 * pc;
+    float cs = 1.0f + t2 * pc;
+    float co, si;
+    switch (q & 3) {
+    case 0: co = cs; si = sn; break;
+    case 1: co = -sn; si = cs; break;
+    case 2: co = -cs; si = -sn; break;
+    default: co = sn; si = -cs; break;
+    }
+    *c_out = co;
+    *s_out = si;
+}
+
+/* Two independent N(0, 1) variates from two Philox words (Box-Muller):
+ * r = sqrt(-2 ln U1) with U1 the fine uniform of w0, angle 2 pi U2 with U2
+ * the grid uniform of w1. */
+void oq_normal_pair(uint32_t w0, uint32_t w1, float *z1, float *z2)
+{
+    float lg = oq_logf(oq_uniform_fine32(w0));
+    float r = sqrtf(-2.0f * lg);
+    float co, si;
+    oq_sincos2pi(oq_uniform24(w1), &co, &si);
+    *z1 = r * co;
+    *z2 = r * si;
+}
+
+float oq_donut_energy(float mu0, float c, float x1, float x2)
+{
+    float sq = x1 * x1 + x2 * x2;
+    float u = sq - mu0;
+    return c * (u * u);
+}
+
+typedef struct {
+    float mu0;        /* ring radius squared */
+    float c;          /* 1 / (2 sigma^2) */
+    int64_t L0;       /* Unbiased budget per partial neighbour set */
+    uint64_t seed;
+    int32_t variant;  /* V_UNBIASED or V_METROPOLIS */
+    int32_t npairs;   /* Unbiased: pairs +-delta per set (the set has 2 npairs points) */
+} oq_donuts_cfg;
+
+typedef struct {
+    double weight;        /* sum of M: original samples */
+    double sum_x[2];      /* sum of M x_i over records (x at the record's start) */
+    double sum_x2[2];
+    double sum_x4[2];
+    double sum_pos[2];    /* sum of M [x_i > 0] */
+    int64_t records, moves, budget_left, period_start;
+    float x[2];           /* state after the run */
+} oq_donuts_stats;
+
+/* One chain for `steps` records from (x1, x2).  Unbiased PNS (Algorithm 7):
+ * the partial neighbour set of a period is {x + d_j, x - d_j : j < npairs}
+ * with d_j ~ N(0, I) drawn when the period starts (SUBSET stream at the
+ * period's first record, Philox block j, words 0 and 1); the proposal is
+ * uniform over the set, so each candidate weighs min(1, exp(-Delta)); M,
+ * the budget and the choice of the next state are those of Algorithm 6.
+ * Metropolis: y = x + d with d ~ N(0, I) from STEP words 0 and 1, accepted
+ * iff ln U (grid uniform of STEP word 3) < -Delta. */
+int oq_donuts_chain(const oq_donuts_cfg *C, uint32_t chain, int64_t steps, float x1, float x2, oq_donuts_stats *S)
+{
+    const int np = C->npairs;
+    const int k = 2 * np;
+    if (C->variant == V_UNBIASED && (np < 1 || np > 64)) return 1;
+    float dx[64], dy[64], dl[128];
+    memset(S, 0, sizeof(*S));
+    int64_t L = C->L0, pstart = 0;
+    int need_set = 1;
+    for (int64_t step = 0; step < steps; ++step) {
+        const float e0 = oq_donut_energy(C->mu0, C->c, x1, x2);
+        double m;
+        float nx1 = x1, nx2 = x2;
+        int moved = 0;
+        if (C->variant == V_METROPOLIS) {
+            float d1, d2;
+            oq_normal_pair(rng_word(C->seed, TAG_STEP, chain, (uint64_t)step, 0),
+                           rng_word(C->seed, TAG_STEP, chain, (uint64_t)step, 1), &d1, &d2);
+            float y1 = x1 + d1, y2 = x2 + d2;
+            float dlt = oq_donut_energy(C->mu0, C->c, y1, y2) - e0;
+            float lu = oq_logf(oq_uniform24(rng_word(C->seed, TAG_STEP, chain, (uint64_t)step, 3)));
+            if (lu < -dlt) {
+                nx1 = y1;
+                nx2 = y2;
+                moved = 1;
+            }
+            m = 1.0;
+        } else {
+            if (need_set) {
+                for (int j = 0; j < np; ++j)
+                    oq_normal_pair(rng_word(C->seed, TAG_SUBSET, chain, (uint64_t)pstart, 4u * (uint32_t)j),
+                                   rng_word(C->seed, TAG_SUBSET, chain, (uint64_t)pstart, 4u * (uint32_t)j + 1u),
+                                   &dx[j], &dy[j]);
+                need_set = 0;
+            }
+            for (int j = 0; j < np; ++j) {
+                dl[2 * j] = oq_donut_energy(C->mu0, C->c, x1 + dx[j], x2 + dy[j]) - e0;
+                dl[2 * j + 1] = oq_donut_energy(C->mu0, C->c, x1 - dx[j], x2 - dy[j]) - e0;
+            }
+            int32_t win, sat;
+            uint64_t sq;
+            float p;
+            int rc = oq_decide(1, NULL, dl, k, 1.0f, C->seed, chain, (uint64_t)step, &win, &sq, &p, &m, &sat);
+            if (rc) return rc;
+            if (m <= (double)L) {
+                L -= (int64_t)m;
+                const int j = win >> 1;
+                if (win & 1) {
+                    nx1 = x1 - dx[j];
+                    nx2 = x2 - dy[j];
+                } else {
+                    nx1 = x1 + dx[j];
+                    nx2 = x2 + dy[j];
+                }
+                moved = 1;
+            } else {
+                m = (double)L;
+                L = C->L0;
+                pstart = step + 1;
+                need_set = 1;
+            }
+        }
+        /* the record weighs the state it starts from */
+        for (int i = 0; i < 2; ++i) {
+            const double xd = (double)(i == 0 ? x1 : x2);
+            const double x2d = xd * xd;
+            S->sum_x[i] += m * xd;
+            S->sum_x2[i] += m * x2d;
+            S->sum_x4[i] += m * (x2d * x2d);
+            if (xd > 0.0) S->sum_pos[i] += m;
+        }
+        S->weight += m;
+        S->records += 1;
+        S->moves += moved;
+        x1 = nx1;
+        x2 = nx2;
+    }
+    S->budget_left = L;
+    S->period_start = pstart;
+    S->x[0] = x1;
+    S->x[1] = x2;
+    return 0;
+}
+
 /* Raw stream access for the RNG pins. */
 void oq_philox(const uint32_t ctr[4], uint32_t k0, uint32_t k1, uint32_t out[4])
 {
@@ -652,6 +824,12 @@ void oq_expf_vec(const float *x, float *y, int64_t n) { for (int64_t i = 0; i < 
 void oq_neg_log1m_vec(const float *x, float *y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = oq_neg_log1m(x[i]); }
 void oq_uniform_fine32_vec(const uint32_t *w, float *y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = oq_uniform_fine32(w[i]); }
 void oq_uniform_fine64_vec(const uint64_t *w, float *y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = oq_uniform_fine64(w[i]); }
+
+void oq_sincos2pi_vec(const float *u, float *c, float *s, int64_t n) { for (int64_t i = 0; i < n; ++i) oq_sincos2pi(u[i], &c[i], &s[i]); }
+void oq_normal_pair_vec(const uint32_t *w0, const uint32_t *w1, float *z1, float *z2, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) oq_normal_pair(w0[i], w1[i], &z1[i], &z2[i]);
+}
 
 /* Unused helper kept private to silence -Wunused for q_entry in some builds. */
 double oq_q_entry(const oq_problem *P, int64_t idx) { return q_entry(P, idx); }

@@ -249,6 +249,52 @@ pns_status pns_restore(pns_ctx *ctx, const void *buf, size_t bytes);
 void pns_destroy(pns_ctx *ctx);
 const char *pns_last_error(void);
 
+/* ---- Continuous state space: Unbiased PNS for continuous targets -------------
+ * Algorithm 7 (Sec. 6) on the Donuts example of Sec. 7:
+ *   pi(x) ~ exp[-(x1^2 + x2^2 - mu0)^2 / (2 sigma^2)] = exp(-E(x)),
+ *   E(x) = c (x1^2 + x2^2 - mu0)^2 with c = 1 / (2 sigma^2),
+ * evaluated in fp32 in this order: s = x1*x1 + x2*x2, u = s - mu0, E = c*(u*u).
+ * PNS_UNBIASED: each period's partial neighbour set is {x + d_j, x - d_j :
+ * j < npairs} with d_j ~ N(0, I) (Box-Muller from the SUBSET Philox stream at
+ * the period's first record, block j, words 0 and 1), so that the set is
+ * reversible; the proposal is uniform over the set, the multiplicity, the
+ * budget L0 and the next state follow Algorithm 6.  PNS_METROPOLIS: the
+ * paper's comparison, y = x + d with d ~ N(0, I), accepted w.p.
+ * min(1, e^{-Delta}).  The chains' records are reduced on the fly to the
+ * multiplicity-weighted sums the paper's bias measures need (Sec. 7). */
+typedef struct {
+    float mu0;                 /* mu0 (the paper: 9) */
+    float c;                   /* 1 / (2 sigma^2) (sigma = 0.1: 50) */
+    int64_t L0;                /* Unbiased: original samples per partial neighbour set (the paper: 1000) */
+    uint64_t seed;             /* Philox key */
+    int32_t variant;           /* PNS_UNBIASED or PNS_METROPOLIS */
+    int32_t npairs;            /* Unbiased: 1..32 pairs +-d per set (the paper: 25, 50 neighbours) */
+    int32_t chain_base;        /* global id of chain 0 (Philox stream id = chain_base + chain), >= 0 */
+    int32_t reserved;          /* must be 0 */
+} pns_donuts_config;
+
+typedef struct {
+    double weight;             /* sum of M over the records: original samples */
+    double sum_x[2];           /* sum of M x_i, x the state each record starts from */
+    double sum_x2[2];          /* sum of M x_i^2 */
+    double sum_x4[2];          /* sum of M x_i^4 */
+    double sum_pos[2];         /* sum of M [x_i > 0] */
+    int64_t records;           /* jump-chain records (Metropolis: steps) */
+    int64_t moves;
+    int64_t budget_left;       /* Unbiased: L after the run */
+    int64_t period_start;      /* Unbiased: record at which the current set was drawn */
+    float x[2];                /* state after the run */
+    int32_t pad[2];
+} pns_donuts_stats;
+
+/* Runs `chains` independent chains for `steps` records each from x0 (chains x 2
+ * floats, host or device; NULL: every chain starts at (sqrt(mu0), 0)) and
+ * writes one pns_donuts_stats per chain to `stats` (host or device).  Works in
+ * device memory it allocates and frees itself; synchronises `stream`.
+ * Fails with PNS_ERR_INVALID_ARG on a bad configuration. */
+pns_status pns_donuts_run(const pns_donuts_config *cfg, int64_t chains, int64_t steps, const float *x0,
+                          pns_donuts_stats *stats, void *stream);
+
 /* Size of the fixed device array that pns_sample_static works in.  Every GPU
  * that loads this library holds it until the process exits. */
 #define PNS_STATIC_SCRATCH_BYTES (16u << 20)

@@ -72,7 +72,7 @@ assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
 
 EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_read_samples", "pns_moments",
            "pns_energy_grads", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore", "pns_destroy",
-           "pns_last_error", "pns_sample_static", "pns_read_best")
+           "pns_last_error", "pns_sample_static", "pns_read_best", "pns_donuts_run")
 STATIC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
@@ -105,6 +105,8 @@ def lib():
         L.pns_sample_static.restype = C.c_int
         L.pns_read_best.argtypes = [vp, vp, vp]
         L.pns_read_best.restype = C.c_int
+        L.pns_donuts_run.argtypes = [vp, C.c_int64, C.c_int64, vp, vp, vp]
+        L.pns_donuts_run.restype = C.c_int
         L.pns_destroy.argtypes = [vp]
         L.pns_destroy.restype = None
         L.pns_last_error.argtypes = []
@@ -386,3 +388,33 @@ class Sampler:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Continuous targets: Unbiased PNS (Algorithm 7) and Metropolis on the Donuts
+# example (Sec. 7).
+# ---------------------------------------------------------------------------
+class pns_donuts_config(C.Structure):
+    _fields_ = [("mu0", C.c_float), ("c", C.c_float), ("L0", C.c_int64), ("seed", C.c_uint64),
+                ("variant", C.c_int32), ("npairs", C.c_int32), ("chain_base", C.c_int32), ("reserved", C.c_int32)]
+
+
+DONUTS_STATS_DTYPE = np.dtype([("weight", np.float64), ("sum_x", np.float64, 2), ("sum_x2", np.float64, 2),
+                               ("sum_x4", np.float64, 2), ("sum_pos", np.float64, 2), ("records", np.int64),
+                               ("moves", np.int64), ("budget_left", np.int64), ("period_start", np.int64),
+                               ("x", np.float32, 2), ("pad", np.int32, 2)])
+
+
+def pns_donuts_run(variant, chains, steps, x0=None, mu0=9.0, c=50.0, L0=1000, seed=0, npairs=25, chain_base=0,
+                   stats=None, stream=None):
+    """Runs the Donuts chains; returns per-chain statistics (a numpy record
+    array of DONUTS_STATS_DTYPE, or fills `stats`, a device buffer of
+    chains * DONUTS_STATS_DTYPE.itemsize bytes)."""
+    cfg = pns_donuts_config(float(np.float32(mu0)), float(np.float32(c)), int(L0), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                            VARIANTS[variant] if isinstance(variant, str) else int(variant), int(npairs),
+                            int(chain_base), 0)
+    out = np.zeros(int(chains), dtype=DONUTS_STATS_DTYPE) if stats is None else stats
+    if x0 is not None and isinstance(x0, np.ndarray):
+        x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    _check(lib().pns_donuts_run(C.byref(cfg), int(chains), int(steps), _addr(x0), _addr(out), _stream(stream)))
+    return out

@@ -46,8 +46,9 @@ def test_struct_sizes_match_header():
 #include <stddef.h>
 #include "pns.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(pns_problem), sizeof(pns_config), sizeof(pns_info), sizeof(pns_stats),
-         offsetof(pns_config, x0), offsetof(pns_stats, energy));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(pns_problem), sizeof(pns_config), sizeof(pns_info),
+         sizeof(pns_stats), offsetof(pns_config, x0), offsetof(pns_stats, energy), sizeof(pns_donuts_config),
+         sizeof(pns_donuts_stats), offsetof(pns_donuts_stats, x));
   return 0;
 }
 """
@@ -58,7 +59,8 @@ int main(void) {
         subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe])
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     want = [C.sizeof(pns.pns_problem), C.sizeof(pns.pns_config), C.sizeof(pns.pns_info), C.sizeof(pns.pns_stats),
-            pns.pns_config.x0.offset, pns.pns_stats.energy.offset]
+            pns.pns_config.x0.offset, pns.pns_stats.energy.offset, C.sizeof(pns.pns_donuts_config),
+            pns.DONUTS_STATS_DTYPE.itemsize, pns.DONUTS_STATS_DTYPE.fields["x"][1]]
     assert got == want
 
 

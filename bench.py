@@ -403,6 +403,70 @@ def fit_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def donuts_workload(args):
+    """Continuous Unbiased PNS (Algorithm 7) on the Donuts target of Sec. 7
+    (mu0 = 9, sigma = 0.1, 50 neighbours, L0 = 1000) against Metropolis with
+    the same N(0, I) proposal: 65,536 chains each; one step = one
+    pns_donuts_run of `--records` records (Unbiased), and Metropolis runs for
+    as many steps as fit in the same GPU time (calibrated on a short run), as
+    the paper compares them at equal time.  Reports records/s, original
+    samples/s and the paper's first-degree bias |mean x1| + |mean x2| per
+    chain, averaged over chains."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    chains = 65536
+    mu0, sigma = 9.0, 0.1
+    c = 1.0 / (2 * sigma * sigma)
+    rng = np.random.default_rng(args.seed)
+    ang = rng.uniform(0, 2 * np.pi, chains)
+    x0 = torch.from_numpy(np.stack([3 * np.cos(ang), 3 * np.sin(ang)], 1).astype(np.float32)).to(dev)
+    out = torch.empty((chains, pns.DONUTS_STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    res = {}
+
+    def per_step_ms(variant, steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pns.pns_donuts_run(variant, chains, steps, x0=x0, mu0=mu0, c=c, L0=1000, seed=7, stats=out)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    per_step_ms("metropolis", 200)  # first launch
+    ratio = per_step_ms("unbiased", 500) / per_step_ms("metropolis", 2000)
+    metro_steps = max(1, int(round(args.records * ratio)))
+    for variant, steps in (("unbiased", args.records), ("metropolis", metro_steps)):
+        for w in range(args.warmup):
+            pns.pns_donuts_run(variant, chains, steps, x0=x0, mu0=mu0, c=c, L0=1000, seed=w, stats=out)
+        ms = []
+        for i in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pns.pns_donuts_run(variant, chains, steps, x0=x0, mu0=mu0, c=c, L0=1000, seed=100 + i, stats=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = np.frombuffer(out.cpu().numpy().tobytes(), dtype=pns.DONUTS_STATS_DTYPE)
+        W = st["weight"]
+        bias1 = float((np.abs(st["sum_x"][:, 0] / W) + np.abs(st["sum_x"][:, 1] / W)).mean())
+        secs = float(np.median(ms)) / 1e3
+        res[variant] = {"records_per_s": chains * steps / secs, "original_samples_per_s": float(W.sum()) / secs,
+                        "ms_per_step": secs * 1e3, "moves_per_record": float(st["moves"].sum()) / (chains * steps),
+                        "first_degree_bias": bias1}
+    line = {"metric": "PNS jump samples/s (records/s)", "workload": "donuts", "value": res["unbiased"]["records_per_s"],
+            "unit": "samples/s", "steps": args.steps, "warmup": args.warmup, "unbiased": res["unbiased"],
+            "metropolis": res["metropolis"],
+            "config": {"workload": "donuts: mu0=9 sigma=0.1, 65536 chains, Unbiased |N|=50 L0=1000 (%d records) vs "
+                                   "Metropolis in the same GPU time (%d steps)" % (args.records, metro_steps)}}
+    print(json.dumps(line), flush=True)
+
+
 def side_workload(args):
     """Other benchmark shapes, one JSON line each (not the headline):
     tempering -- 512 fp32 instances, n uniform in [128, 2048], 8 replicas on a
@@ -433,6 +497,8 @@ def side_workload(args):
         row_bytes = 4 * ns
         desc = ("tempering: %d fp32 instances n~U[128,2048], 8 replicas (beta 0.1..10), Unbiased k=n/16, "
                 "swap every 100 original samples, 1000 original samples per chain per step" % n_inst)
+    elif args.workload == "donuts":
+        return donuts_workload(args)
     elif args.workload == "fit":
         return fit_workload(args)
     else:
@@ -496,7 +562,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="heuristic chain-to-CTA mapping")
     ap.add_argument("--quick", action="store_true", help="skip the Basic / plain side measurements")
-    ap.add_argument("--workload", default="dense1024", choices=["dense1024", "tempering", "lattice", "fit"])
+    ap.add_argument("--workload", default="dense1024", choices=["dense1024", "tempering", "lattice", "fit", "donuts"])
     ap.add_argument("--instances", type=int, default=512)
     args = ap.parse_args()
     if args.workload != "dense1024":

@@ -213,16 +213,17 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
     // The set's sub-block, b and diagonal, by cp.async (4-byte entries) or
     // plain loads (2-byte entries).
     auto load_set = [&](int s) {
-        const int kk = k * k;
-        for (int idx = gtid; idx < kk; idx += GT) {
-            const int a = idx / k, t = idx - a * k;
+        for (int a = wg; a < k; a += W) {  // row a of the sub-block by warp, columns by lane
             int ra = s + a;
             if (ra >= n) ra -= n;
-            int ct = s + t;
-            if (ct >= n) ct -= n;
-            const QT *src = Q + static_cast<int64_t>(ra) * ld + ct;
-            if constexpr (sizeof(QT) == 4) cp_async4(sub + idx, src);
-            else sub[idx] = *src;
+            const QT *row = Q + static_cast<int64_t>(ra) * ld;
+            QT *dst = sub + a * k;
+            for (int t = lane; t < k; t += 32) {
+                int ct = s + t;
+                if (ct >= n) ct -= n;
+                if constexpr (sizeof(QT) == 4) cp_async4(dst + t, row + ct);
+                else dst[t] = row[ct];
+            }
         }
         for (int t = gtid; t < k; t += GT) {
             int ct = s + t;
@@ -461,17 +462,25 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
                 __syncwarp();
             }
             gsync();
-            if (gtid == 0) {
-                // records per temperature in this period, then the exchange
-                int rec_b[16];
-                for (int s = 0; s < R; ++s) rec_b[cst(s)->beta_idx] = *sc32(s, 4);
+            if (wg == 0) {
+                // warp 0 of the group, one lane per chain / pair: records per
+                // temperature in this period, the exchange, the next queue
+                // (small arrays in shared memory: local arrays would live in
+                // cold local memory)
+                int32_t *rec_b = q_order + 20;   // [16] records of temperature b
+                int32_t *slot_of = rec_b + 16;   // [16] chain holding temperature b
+                if (lane < R) {
+                    const int b = cst(lane)->beta_idx;
+                    rec_b[b] = *sc32(lane, 4);
+                    slot_of[b] = lane;
+                }
+                __syncwarp();
                 if (pr + 1 == per_round) {
                     const uint64_t ndone = static_cast<uint64_t>(cst(0)->sum_m) / static_cast<uint64_t>(P.swap_interval);
                     const uint64_t rnd = ndone - 1;
-                    int slot_of[16];
-                    for (int s = 0; s < R; ++s) slot_of[cst(s)->beta_idx] = s;
-                    int q = 0;
-                    for (int a = static_cast<int>(rnd & 1u); a + 1 < R; a += 2, ++q) {
+                    // pairs (a, a + 1), a = rnd mod 2 + 2q, are disjoint: pair q on lane q
+                    const int a = static_cast<int>(rnd & 1u) + 2 * lane;
+                    if (a + 1 < R) {
                         const int sa_ = slot_of[a], sb_ = slot_of[a + 1];
                         ChainState *pa = cst(sa_);
                         ChainState *pb = cst(sb_);
@@ -479,31 +488,31 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
                         const float de = __double2float_rn(__dsub_rn(pa->E, pb->E));
                         const float xr = __fmul_rn(db, de);
                         const uint32_t w = rng_word(seed, TAG_SWAP, static_cast<uint32_t>(chd0.group) + P.group_base,
-                                                    rnd, static_cast<uint32_t>(q));
+                                                    rnd, static_cast<uint32_t>(lane));
                         if (det_logf(u01_grid(w)) < xr) {
                             pa->beta_idx = a + 1;
                             pb->beta_idx = a;
-                            slot_of[a] = sb_;
-                            slot_of[a + 1] = sa_;
                             pa->swaps += 1;
                             pb->swaps += 1;
                         }
                     }
+                    __syncwarp();
                 }
-                // next queue: chains by the records their new temperature took, most first
-                int key[16];
-                for (int s = 0; s < R; ++s) {
-                    key[s] = rec_b[cst(s)->beta_idx];
-                    q_order[s] = s;
-                }
-                for (int a = 1; a < R; ++a)
-                    for (int b = a; b > 0 && key[q_order[b]] > key[q_order[b - 1]]; --b) {
-                        const int t = q_order[b];
-                        q_order[b] = q_order[b - 1];
-                        q_order[b - 1] = t;
+                // next queue: chains by the records their (new) temperature took,
+                // most first, ties by chain: the rank of chain `lane`
+                if (lane < R) {
+                    const int key = rec_b[cst(lane)->beta_idx];
+                    int rank = 0;
+                    for (int s2 = 0; s2 < R; ++s2) {
+                        const int k2 = rec_b[cst(s2)->beta_idx];
+                        rank += (k2 > key || (k2 == key && s2 < lane)) ? 1 : 0;
                     }
-                *q_next = 0;
-                *q_running = R;
+                    q_order[rank] = lane;
+                }
+                if (lane == 0) {
+                    *q_next = 0;
+                    *q_running = R;
+                }
             }
             if (!last) load_set(sn);  // the sub-block is not read until the next period
             // the chain(s) that ended last, by the whole group

@@ -138,8 +138,8 @@ PNS_HD BlockSmem block_smem(int32_t ld, int32_t k, int32_t hbytes, int32_t qbyte
     s.chain_bytes = s.scratch + 32;  // log length, records, finalised flag, set start, first step
     s.sub = R * s.chain_bytes;
     s.bd = s.sub + round16(k * k * qbytes);  // b, then diag, of the set: 4-byte entries, 16-byte aligned
-    s.ctrl = s.bd + 2 * round16(4 * k);      // queue order[16], next, running
-    s.group_bytes = s.ctrl + 80;
+    s.ctrl = s.bd + 2 * round16(4 * k);      // queue order[16], next, running, pad[2], records and slot by temperature [16] each
+    s.group_bytes = s.ctrl + 208;
     return s;
 }
 

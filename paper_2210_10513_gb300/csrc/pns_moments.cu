@@ -33,6 +33,7 @@ constexpr int B_SLAB_BYTES = 64 * 16 * 2;   // 64 rows x 16 bf16
 constexpr int STAGE_BYTES = 3 * 4 * A_SLAB_BYTES + 4 * B_SLAB_BYTES;  // 56 KiB
 constexpr int TMEM_COLS = 256;        // three 64-column fp32 accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr int MOM_THREADS = 512;      // 16 warps build the operand tiles
 
 // Shared-memory matrix descriptor (no swizzle, K-major core matrices of 8 rows
 // x 16 bytes): start address, K-direction core-matrix stride (leading byte
@@ -154,11 +155,12 @@ __global__ void scalar_final_kernel(const double *partials, int blocks, double *
 }
 
 // ---------------------------------------------------------------------------
-// The tensor-core contraction.  128 threads; each CTA takes up to 16384
+// The tensor-core contraction.  512 threads; each CTA takes up to 16384
 // samples in stages of 64, double-buffered: while the tensor cores work on one
-// stage the threads build the next one.
+// stage the threads build the next one (the build, not the MMA, sets the pace,
+// so all 16 warps take part in it).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1) moments_tc_kernel(SampleSrc src, const double *centre, float *partials,
+__global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc src, const double *centre, float *partials,
                                                             int32_t *status) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *stage_buf[2] = {sm, sm + STAGE_BYTES};
@@ -192,6 +194,23 @@ __global__ void __launch_bounds__(128, 1) moments_tc_kernel(SampleSrc src, const
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    // One sample per thread of the first 64, held in registers one stage
+    // ahead so that its global loads overlap the build of the current stage.
+    double nx_m = 0.0, nx_e = 0.0;
+    uint32_t nx_x0 = 0u, nx_x1 = 0u;
+    bool nx_valid = false;
+    auto load_sample = [&](int g) {
+        const int64_t s = s_begin + static_cast<int64_t>(g) * STAGE_K + tid;
+        nx_valid = g < stages && s < s_end;
+        if (nx_valid) {
+            const int64_t row = sample_row(src, s);
+            nx_m = src.tape_m[row];
+            nx_e = src.tape_E[row];
+            nx_x0 = src.tape_x[row * src.W];
+            nx_x1 = src.W > 1 ? src.tape_x[row * src.W + 1] : 0u;
+        }
+    };
+    if (tid < STAGE_K) load_sample(0);
     int committed = 0;  // stages whose MMAs were issued
     for (int g = 0; g < stages; ++g) {
         const int buf = g & 1;
@@ -204,27 +223,22 @@ __global__ void __launch_bounds__(128, 1) moments_tc_kernel(SampleSrc src, const
         }
         __syncthreads();
         if (*fail) break;
-        // stage the 64 samples: six weight planes and the bits
+        // stage the 64 samples (loaded during the previous stage): six weight
+        // planes and the bits; then start the loads of the next stage
         if (tid < STAGE_K) {
-            const int64_t s = s_begin + static_cast<int64_t>(g) * STAGE_K + tid;
             uint16_t pw[6] = {0, 0, 0, 0, 0, 0};
-            uint32_t x0 = 0u, x1 = 0u;
-            if (s < s_end) {
-                const int64_t row = sample_row(src, s);
-                const double m = src.tape_m[row];
-                const double e = src.tape_E[row];
-                split3(static_cast<float>(m), pw);
-                split3(static_cast<float>(m * (e - c)), pw + 3);
-                x0 = src.tape_x[row * src.W];
-                x1 = src.W > 1 ? src.tape_x[row * src.W + 1] : 0u;
+            if (nx_valid) {
+                split3(static_cast<float>(nx_m), pw);
+                split3(static_cast<float>(nx_m * (nx_e - c)), pw + 3);
             }
             for (int p = 0; p < 6; ++p) planes[p * STAGE_K + tid] = pw[p];
-            bits[2 * tid] = x0;
-            bits[2 * tid + 1] = x1;
+            bits[2 * tid] = nx_valid ? nx_x0 : 0u;
+            bits[2 * tid + 1] = nx_valid ? nx_x1 : 0u;
+            load_sample(g + 1);
         }
         __syncthreads();
         // A chunks: (mma m, row r, octet o) -> 8 bf16 along the sample axis
-        for (int cidx = tid; cidx < 3 * 128 * 8; cidx += 128) {
+        for (int cidx = tid; cidx < 3 * 128 * 8; cidx += MOM_THREADS) {
             const int m = cidx / (128 * 8);
             const int rem = cidx - m * 128 * 8;
             const int r = rem >> 3;
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(128, 1) moments_tc_kernel(SampleSrc src, const
             *reinterpret_cast<uint4 *>(sb + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
         // B chunks: (row j, octet o) -> bits as bf16 1.0 / 0
-        for (int cidx = tid; cidx < 64 * 8; cidx += 128) {
+        for (int cidx = tid; cidx < 64 * 8; cidx += MOM_THREADS) {
             const int j = cidx >> 3;
             const int o = cidx & 7;
             uint32_t packed[4];
@@ -302,13 +316,17 @@ __global__ void __launch_bounds__(128, 1) moments_tc_kernel(SampleSrc src, const
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool ok = *fail == 0 && committed == stages;
     if (ok) {
-        // warp w reads TMEM lanes 32w .. 32w + 31 (rows of the accumulators)
-        const int lane_row = 32 * warp + (tid & 31);
+        // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows of the
+        // accumulators); the four warps of a lane quarter split the columns
+        const int quarter = warp & 3;
+        const int lane_row = 32 * quarter + (tid & 31);
         float *dst = partials + static_cast<int64_t>(blockIdx.x) * 3 * 128 * 64;
-        for (int m = 0; m < 3; ++m) {
-            for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int blk = warp >> 2; blk < 12; blk += MOM_THREADS / 128) {
+            const int m = blk >> 2;
+            const int c0 = (blk & 3) * 16;
+            {
                 uint32_t v[16];
-                const uint32_t ta = tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(m * 64 + c0);
+                const uint32_t ta = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(m * 64 + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                     "%13, %14, %15}, [%16];"
@@ -443,7 +461,7 @@ cudaError_t launch_moments(const uint32_t *tape_x, const double *tape_m, const d
         const int smem = 2 * STAGE_BYTES + 2048;
         e = cudaFuncSetAttribute(moments_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        moments_tc_kernel<<<static_cast<unsigned>(ctas), 128, smem, s>>>(src, centre, partials, status);
+        moments_tc_kernel<<<static_cast<unsigned>(ctas), MOM_THREADS, smem, s>>>(src, centre, partials, status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

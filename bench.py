@@ -337,7 +337,8 @@ def gpu_arm(args):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
         "clocks": clk.summary(), "wall_s": wall,
         "mapping": {"warps_per_chain": info.warps_per_chain, "team_warps": info.team_warps,
-                    "producer_warps": info.producer_warps, "spec_depth": info.spec_depth, "ctas": info.ctas,
+                    "producer_warps": info.producer_warps, "spec_depth": info.spec_depth,
+                    "set_sweep": info.set_sweep, "ctas": info.ctas,
                     "autotune": not args.no_autotune,
                     "cuda_graph": True},
     }

@@ -144,6 +144,9 @@ typedef struct {
     int32_t spec_depth;        /* speculative kernel: records evaluated at once (0: not used) */
     int32_t period_blocked;    /* 1: period-blocked update (Unbiased PNS with exchange): set fields
                                   from the k x k sub-block, other fields once per period */
+    int32_t set_sweep;         /* 1: set-sweep kernel (Unbiased PNS, systematic sets): the
+                                  spec_depth warps of a chain evaluate every set of the current
+                                  state once, then decide up to 32 * spec_depth records at once */
 } pns_info;
 
 typedef struct {

@@ -63,6 +63,7 @@ struct pns_ctx {
     int fmt = 0, qtype = 0, is_float = 0, hbytes = 4, T = 1, prod = 0;
     int spec = 0;  // > 0: speculative kernel with this many warps (records) per chain
     bool blocked = false;  // period-blocked kernel
+    bool sweep = false;    // with spec > 0: the set-sweep kernel (spec warps per chain)
     int gw = 1;            // blocked kernel: warps per exchange group
     std::vector<InstHost> inst;
     int32_t max_ld = 32, LD = 32, W = 1;
@@ -212,6 +213,7 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     for (int64_t i = 0; i < c.chains; i += R) {
         const InstHost &ih = c.inst[chains[i].inst];
         const int32_t per = c.blocked   ? block_chain_bytes(ih.ld, ih.k, c.hbytes, c.qtype == PNS_Q_I16 ? 2 : 4, R)
+                            : c.spec > 0 && c.sweep ? sweep_chain_bytes(ih.ld, ih.n, ih.k, c.hbytes, c.spec)
                             : c.spec > 0 ? spec_chain_bytes(ih.ld, ih.k, c.hbytes, list, c.spec)
                                          : chain_smem(ih.ld, ih.k, c.hbytes, list, c.prod > 0, slot_list).total;
         units.push_back({static_cast<int32_t>(i), R, per * R});
@@ -373,6 +375,7 @@ static int auto_warps(const pns_ctx &c) {
 // A chain-to-CTA mapping: warps per chain, producer warps, speculation depth.
 struct Mapping {
     int T = 1, prod = 0, spec = 0, per_cta = 0, block = 0, gw = 0;  // gw 0: chosen by the planner
+    int sweep = 0;  // with spec: the set-sweep kernel
 };
 
 // The period-blocked kernel: Unbiased PNS, systematic sets, exchange, dense Q, k <= 128.
@@ -388,6 +391,15 @@ static bool spec_allowed(const pns_ctx &c) {
     for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
     return c.fmt == PNS_DENSE && c.cfg.swap_interval == 0 && c.cfg.L0 < (1ll << 31) && kmax <= 128 &&
            (c.cfg.variant == PNS_UNBIASED || c.cfg.variant == PNS_METROPOLIS);
+}
+
+// The set-sweep kernel with D warps per chain: Unbiased PNS, systematic sets,
+// every instance with at most 4 D sets.
+static bool sweep_allowed(const pns_ctx &c, int D) {
+    if (!spec_allowed(c) || c.cfg.variant != PNS_UNBIASED || c.cfg.subset != PNS_SUBSET_SYSTEMATIC) return false;
+    for (const InstHost &ih : c.inst)
+        if (!sweep_supported(c.qtype, D, ih.n, ih.k)) return false;
+    return true;
 }
 
 // The heuristic mapping (and the environment overrides used by the tests).
@@ -425,6 +437,9 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
     if (m.spec > 0 && !spec_allowed(c)) m.spec = 0;
     if (cfg->track_best) m.spec = 0;  // X_max is kept by the per-flip kernel
     if (m.spec > 0) m.prod = 0;
+    m.sweep = 0;
+    if (const char *e = getenv("PNS_SWEEP")) m.sweep = atoi(e) ? 1 : 0;
+    if (m.sweep && !(m.spec > 0 && sweep_allowed(c, m.spec))) m.sweep = 0;
     // Period blocking takes the dependent row loads off the record chain of
     // every exchange group (whose hottest replica sets the pace).
     m.block = block_allowed(c) && cfg->warps_per_chain <= 1 && !cfg->track_best ? 1 : 0;
@@ -447,6 +462,7 @@ static pns_status apply_mapping(pns_ctx *c, Mapping m, cudaStream_t s) {
         c->T = m.T;
         c->prod = m.prod;
         c->spec = m.spec;
+        c->sweep = m.spec > 0 && m.sweep != 0;
         c->blocked = m.block != 0;
         pl = PlanOut();
         if (c->blocked) {
@@ -535,8 +551,8 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
                 if (!bar) continue;
                 if (std::string(line, bar - line) == key) {
                     Mapping m;
-                    if (sscanf(bar + 1, "%d %d %d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta, &m.block, &m.gw) ==
-                        6) {
+                    if (sscanf(bar + 1, "%d %d %d %d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta, &m.block, &m.gw,
+                               &m.sweep) == 7) {
                         fclose(f);
                         return apply_mapping(c, m, s);
                     }
@@ -557,11 +573,12 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         if (T_fixed > 0 && (m.T != T_fixed || m.spec > 0)) return;
         if (!sampler_supported(c->fmt, c->qtype, c->hbytes, m.T)) return;
         if (m.spec > 0 && (!spec_allowed(*c) || !spec_supported(c->qtype, m.spec))) return;
+        if (m.sweep && (m.spec <= 0 || !sweep_allowed(*c, m.spec))) return;
         if (m.block && (!block_allowed(*c) || m.T != 1)) return;
         if (c->cfg.track_best && (m.block || m.spec > 0)) return;
         for (const Mapping &o : cands)
             if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta && o.block == m.block &&
-                o.gw == m.gw)
+                o.gw == m.gw && o.sweep == m.sweep)
                 return;
         cands.push_back(m);
     };
@@ -570,6 +587,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
             for (int prod = 0; prod <= 3; ++prod) add(Mapping{T, prod, 0, c->per_cta});
         add(Mapping{8, 0, 0, c->per_cta});
         for (int d : {4, 8, 16}) add(Mapping{1, 0, d, c->per_cta});
+        add(Mapping{1, 0, 8, c->per_cta, 0, 0, 1});
         for (int gw : {0, c->R, (c->R + 1) / 2, (c->R + 3) / 4}) add(Mapping{1, 0, 0, c->per_cta, 1, gw});
     } else {
         for (int T : Ts_csr) add(Mapping{T, 0, 0, c->per_cta});
@@ -644,8 +662,8 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
     if (code != 0) return fail(static_cast<pns_status>(code), "device error while autotuning");
     if (path) {
         if (FILE *f = fopen(path, "a")) {
-            fprintf(f, "%s|%d %d %d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta, best.block,
-                    best.gw);
+            fprintf(f, "%s|%d %d %d %d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta, best.block,
+                    best.gw, best.sweep);
             fclose(f);
         }
     }
@@ -671,6 +689,7 @@ pns_status pns_get_info(const pns_ctx *ctx, pns_info *info) {
     info->team_warps = ctx->blocked ? ctx->gw : (ctx->spec > 0 ? 0 : ctx->T);
     info->producer_warps = ctx->spec > 0 ? 0 : ctx->prod;
     info->spec_depth = ctx->spec;
+    info->set_sweep = ctx->sweep ? 1 : 0;
     info->period_blocked = ctx->blocked ? 1 : 0;
     return PNS_OK;
 }
@@ -1011,6 +1030,11 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.group_base = static_cast<uint32_t>(c->cfg.group_base);
     auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {
         if (c->blocked) return launch_block(c->qtype, Pl, grid, c->n_threads, c->smem, s);
+        if (c->spec > 0 && c->sweep) {
+            int max_sets = 1;
+            for (const InstHost &ih : c->inst) max_sets = std::max(max_sets, sweep_sets(ih.n, ih.k));
+            return launch_sweep(c->qtype, max_sets, Pl, grid, c->n_threads, c->smem, s);
+        }
         if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->n_threads, c->smem, s);
         return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->n_threads, c->smem, s);
     };

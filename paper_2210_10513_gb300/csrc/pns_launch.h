@@ -44,6 +44,15 @@ bool spec_supported(int qtype, int D);
 cudaError_t launch_spec(int qtype, int D, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
 int32_t spec_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, bool list, int32_t D);
 
+// Set-sweep kernel for Unbiased PNS with systematic sets on dense Q: 8 warps
+// per chain evaluate all n / gcd(n, k) sets of the current state (at most
+// 32), then decide up to 256 records at once.
+int sweep_sets(int n, int k);
+bool sweep_supported(int qtype, int D, int n, int k);
+cudaError_t launch_sweep(int qtype, int max_sets, const KParams &P, int grid, int block, size_t smem,
+                         cudaStream_t s);
+int32_t sweep_chain_bytes(int32_t ld, int32_t n, int32_t k, int32_t hbytes, int32_t D);
+
 // Period-blocked kernel for Unbiased PNS with systematic sets and replica
 // exchange on dense Q (k <= 128): one warp per chain, the group's set
 // sub-block in shared memory, logged rows applied at period ends.

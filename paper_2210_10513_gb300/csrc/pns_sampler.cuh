@@ -199,13 +199,19 @@ __device__ __forceinline__ float u64_to_f32_rn(uint64_t v) {
     return __fmul_rn(__uint2float_rn(m), pow2f(sh));
 }
 
-// anchor_f = e^{-beta A} (1 when A = 0), computed by the caller as soon as the
-// anchor is known.
-__device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anchor_f, float e1) {
-    Mult r;
+// The multiplicity splits into a part fixed by the state and the set (the
+// move probability p = S 2^-32 / k * e^{-beta A}, and -ln(1 - p)) and a part
+// drawn per record (the Exp(1) e1): M = 1 + floor(e1 / -ln(1 - p)), i.e.
+// 1 + Geom(p).  anchor_f = e^{-beta A} (1 when A = 0).
+__device__ __forceinline__ float mult_p(uint64_t S, int32_t k, float anchor_f) {
     float ps = __fmul_rn(u64_to_f32_rn(S), 0x1p-32f);
     ps = __fdiv_rn(ps, __int2float_rn(k));
-    const float p = __fmul_rn(ps, anchor_f);
+    return __fmul_rn(ps, anchor_f);
+}
+
+// M from p, c = -ln(1 - p) (read only when 0 < p < 1) and e1.
+__device__ __forceinline__ Mult mult_from(float p, float c, float e1) {
+    Mult r;
     r.sat = 0;
     r.fgl = 0.0f;
     if (p >= 1.0f) {
@@ -218,7 +224,7 @@ __device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anc
         r.fgl = __int_as_float(0x7f800000);
         return r;
     }
-    const float g = __fdiv_rn(e1, det_neg_log1m(p));
+    const float g = __fdiv_rn(e1, c);
     if (!(g < 0x1p63f)) {
         r.sat = 1;
         r.mi = -1;
@@ -233,6 +239,12 @@ __device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anc
         r.fgl = fg;
     }
     return r;
+}
+
+__device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anchor_f, float e1) {
+    const float p = mult_p(S, k, anchor_f);
+    if (p >= 1.0f || p <= 0.0f) return mult_from(p, 1.0f, e1);
+    return mult_from(p, det_neg_log1m(p), e1);
 }
 
 // First k distinct values of v_m = floor(word_m n / 2^32), m = 0, 1, ...,

@@ -1,0 +1,53 @@
+// pns_sweep_dense.cu -- instantiations of the set-sweep kernel (dense Q):
+// 8 warps per chain, 1, 2 or 4 sets per warp.
+#include "pns_launch.h"
+#include "pns_sweep.cuh"
+
+namespace pnsk {
+
+constexpr int SWEEP_WARPS = 8;
+
+template <typename QT, typename HT, int SPW>
+static cudaError_t launch_sweep_t(const KParams &P, int grid, int block, size_t smem, cudaStream_t s) {
+    auto kern = pns_sweep_kernel<QT, HT, SWEEP_WARPS, SPW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <typename QT, typename HT>
+static cudaError_t sweep_by_spw(int spw, const KParams &P, int grid, int block, size_t smem, cudaStream_t s) {
+    switch (spw) {
+    case 1: return launch_sweep_t<QT, HT, 1>(P, grid, block, smem, s);
+    case 2: return launch_sweep_t<QT, HT, 2>(P, grid, block, smem, s);
+    case 4: return launch_sweep_t<QT, HT, 4>(P, grid, block, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int sweep_sets(int n, int k) { return n / gcd32(n, k); }
+
+bool sweep_supported(int qtype, int D, int n, int k) {
+    if (!((qtype == 0 || qtype == 1 || qtype == 2) && D == SWEEP_WARPS)) return false;
+    if (k < 1 || k > 128 || k > n) return false;
+    return sweep_sets(n, k) <= 4 * SWEEP_WARPS;
+}
+
+cudaError_t launch_sweep(int qtype, int max_sets, const KParams &P, int grid, int block, size_t smem,
+                         cudaStream_t s) {
+    const int spw = max_sets <= SWEEP_WARPS ? 1 : max_sets <= 2 * SWEEP_WARPS ? 2 : 4;
+    switch (qtype) {
+    case 0: return sweep_by_spw<int16_t, int32_t>(spw, P, grid, block, smem, s);
+    case 1: return sweep_by_spw<int32_t, int32_t>(spw, P, grid, block, smem, s);
+    case 2: return sweep_by_spw<float, float>(spw, P, grid, block, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int32_t sweep_chain_bytes(int32_t ld, int32_t n, int32_t k, int32_t hbytes, int32_t D) {
+    (void)D;
+    return sweep_smem(ld, hbytes, k, sweep_sets(n, k)).total;
+}
+
+}  // namespace pnsk

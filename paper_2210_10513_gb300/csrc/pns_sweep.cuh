@@ -8,12 +8,12 @@
 // quantised sum and the move probability p (Algorithm 6 with the uniform
 // proposal, Eq. for Q_i).  This kernel evaluates all I sets of the current
 // state once -- the D warps of a chain own I / D sets each and leave p,
-// -ln(1 - p) and the weights in shared memory -- and then warp 0 alone
+// -ln(1 - p) and the weights in shared memory -- and then one warp alone
 // decides the records 32 at a time: record r lies on set (s0 + r) mod I, its
 // budget is the current L for r = 0 and L0 after a stay, and it moves iff its
 // multiplicity 1 + Geom(p) fits the budget.  Stays are committed in closed
 // form without a barrier; the first mover's race (Proposition 5) reads its
-// set's weights, and warp 0 applies the row before the team evaluates the
+// set's weights, and that warp applies the row before the team evaluates the
 // new state.  The other warps wait at the barrier meanwhile, so the issue
 // slots of the SM go to the chains that need them.  The records are
 // bit-identical to one-at-a-time evaluation: every decision uses the same
@@ -64,6 +64,9 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     const int tid = threadIdx.x - team * TT;
     const int lane = threadIdx.x & 31;
     const int w = tid >> 5;
+    // the warp that decides the records: warp `team & 3`, so that the serial
+    // warps of the chains sharing a CTA sit on different warp schedulers
+    const int wser = team & 3;
     const int cid = P.cta_chains[cd.first + team];
     const ChainDesc chd = P.chain[cid];
     const InstDesc in = P.inst[chd.inst];
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
             reinterpret_cast<uint4 *>(h)[c] = reinterpret_cast<const uint4 *>(gh)[c];
         for (int q = tid; q < ld / 32; q += TT) xw[q] = gx[q];
     }
-    ChainState st = P.state[cid];  // (kept by warp 0; the state of its lane 0 is written back)
+    ChainState st = P.state[cid];  // (kept by warp wser; the state of its lane 0 is written back)
     const float beta = in.betas[st.beta_idx];
     const uint64_t seed = P.seed;
     const uint32_t chain_id = static_cast<uint32_t>(cid) + P.chain_base;
@@ -142,15 +145,8 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 }
             }
             D_t amin[SPW];
-            float anchor_f[SPW];
 #pragma unroll
             for (int u = 0; u < SPW; ++u) amin[u] = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin[u]));
-#pragma unroll
-            for (int u = 0; u < SPW; ++u) {
-                const float af = A::tof(amin[u]);
-                const float anchor_e = det_expf(-__fmul_rn(beta, af));
-                anchor_f[u] = af > 0.0f ? anchor_e : 1.0f;
-            }
             uint32_t sa[SPW], sb[SPW];
 #pragma unroll
             for (int u = 0; u < SPW; ++u) {
@@ -169,19 +165,32 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                     }
                 }
             }
+            // the per-set scalars, lane u for set u: anchor e^{-beta A},
+            // p and -ln(1 - p)
+            float af = 0.0f;
+            uint64_t S = 0;
+            int my_sg = 0;
+            bool my_own = false;
 #pragma unroll
             for (int u = 0; u < SPW; ++u) {
                 const uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa[u]);
                 const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb[u]);
-                const uint64_t S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
-                const float p = mult_p(S, k, anchor_f[u]);
-                const float c = det_neg_log1m(p);  // (used only when 0 < p < 1)
-                if (own[u] && lane == 0) table[sg[u]] = make_float2(p, c);
+                if (lane == u) {
+                    af = A::tof(amin[u]);
+                    S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
+                    my_sg = sg[u];
+                    my_own = own[u];
+                }
             }
+            const float anchor_e = det_expf(-__fmul_rn(beta, af));
+            const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
+            const float p = mult_p(S, k, anchor_f);
+            const float c = det_neg_log1m(p);  // (used only when 0 < p < 1)
+            if (lane < SPW && my_own) table[my_sg] = make_float2(p, c);
         }
         sync_team();
-        // ---- warp 0: records 32 at a time up to the first mover -------------
-        if (w == 0) {
+        // ---- warp wser: records 32 at a time up to the first mover ----------
+        if (w == wser) {
             bool moved = false;
             while (!moved && done < P.steps) {
                 const int64_t left = P.steps - done;
@@ -208,6 +217,10 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 const int nstay = first;
                 int j = -1, mi = 0, sat = 0;
                 D_t dj = 0;
+                constexpr int VE = 16 / static_cast<int>(sizeof(QT));
+                constexpr int PRE = 4;
+                const int chunks = ld / VE;
+                uint4 pre[PRE];  // the mover's row: its first chunks are loaded ahead of the bookkeeping
                 if (moved) {
                     mi = __shfl_sync(0xFFFFFFFFu,
                                      static_cast<int32_t>(mu.mi >= 0 ? mu.mi : static_cast<int64_t>(mu.fgl) + 1), first);
@@ -241,6 +254,10 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                     j = sf * g + r0 + static_cast<int>(wpos);
                     j = j >= n ? j - n : j;
                     dj = delta_of(j);
+                    const QT *row = Q + static_cast<int64_t>(j) * ld;
+#pragma unroll
+                    for (int u = 0; u < PRE; ++u)
+                        if (lane + 32 * u < chunks) pre[u] = ld_nc_v4(row + (lane + 32 * u) * VE);
                 }
                 // tape: record r stays with M = its budget, or is the mover
                 if (P.tape == 2) {
@@ -278,10 +295,11 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                     if (sat) st.saturated += 1;
                     st.flips += 1;
                     const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
-                    constexpr int VE = 16 / static_cast<int>(sizeof(QT));
                     const QT *row = Q + static_cast<int64_t>(j) * ld;
-                    const int chunks = ld / VE;
-                    int c = lane;
+#pragma unroll
+                    for (int u = 0; u < PRE; ++u)
+                        if (lane + 32 * u < chunks) add_chunk<QT, HT>(h + (lane + 32 * u) * VE, pre[u], up);
+                    int c = lane + 32 * PRE;
                     for (; c + 3 * 32 < chunks; c += 4 * 32) {
                         const uint4 v0 = ld_nc_v4(row + (c + 0 * 32) * VE);
                         const uint4 v1 = ld_nc_v4(row + (c + 1 * 32) * VE);
@@ -293,13 +311,12 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                         add_chunk<QT, HT>(h + (c + 3 * 32) * VE, v3, up);
                     }
                     for (; c < chunks; c += 32) add_chunk<QT, HT>(h + c * VE, ld_nc_v4(row + c * VE), up);
-                    __syncwarp();
+                    __syncwarp();  // (every lane has read x_j)
                     if (lane == 0) {
                         xw[j >> 5] ^= 1u << (j & 31);
                         st.E = __dadd_rn(st.E, A::tod(dj));
                         st.best_E = fmin(st.best_E, st.E);
                     }
-                    __syncwarp();
                 }
                 st.step += ncommit;
                 tape_pos += ncommit;
@@ -308,7 +325,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
             if (lane == 0) ctl[0] = static_cast<int32_t>(done < P.steps);
         }
         sync_team();
-        if (!ctl[0]) break;  // (warp 0 writes ctl again only after the next evaluation's barrier)
+        if (!ctl[0]) break;  // (ctl is written again only after the next evaluation's barrier)
     }
 
     // ---- write back ---------------------------------------------------------
@@ -320,7 +337,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
             reinterpret_cast<uint4 *>(gh)[c] = reinterpret_cast<const uint4 *>(h)[c];
         for (int q = tid; q < ld / 32; q += TT) gx[q] = xw[q];
     }
-    if (tid == 0) {
+    if (tid == 32 * wser) {
         st.sum_m = __dadd_rn(st.sum_m, static_cast<double>(sum_int));
         st.tape_records = P.tape ? (tape_pos < P.tape_cap ? tape_pos : P.tape_cap) : 0;
         P.state[cid] = st;

@@ -313,10 +313,15 @@ def gpu_arm(args):
     flips_per_launch = d["flips"] / max(1, args.steps) / max(1, world)
     avg_launch_s = kernel_s / max(1, args.steps)
     achieved = flips_per_launch * ROW_BYTES / avg_launch_s / 1e9
+    # DRAM bytes per launch from one ncu capture of the kernel this mapping
+    # runs (null when the capture was of another kernel)
     traffic = None
+    kernel = "pns_sweep_kernel" if info.set_sweep else ("pns_spec_kernel" if info.spec_depth else "pns_sample_kernel")
     tr_path = os.path.join(ROOT, "profiles", "traffic_dense_int16_n1024.json")
     if os.path.exists(tr_path):
-        traffic = json.load(open(tr_path)).get("dram_bytes_per_launch")
+        tr = json.load(open(tr_path))
+        if tr.get("kernel", "").startswith(kernel):
+            traffic = tr.get("dram_bytes_per_launch")
     cpu = None
     if world == 1 and not args.no_cpu:
         from oracle import build_oracle

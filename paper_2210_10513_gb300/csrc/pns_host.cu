@@ -88,6 +88,8 @@ struct pns_ctx {
     uint32_t *d_tape_x = nullptr;   // tape = 2
     double *d_tape_E = nullptr;
     uint32_t *d_xbest = nullptr;    // track_best: X_max per chain (W words)
+    float4 *d_wtab = nullptr;       // integer Q without exchange: weight tables per distinct beta
+    int2 *d_wtab_desc = nullptr;
     int64_t tape_alloc = 0;  // records per chain allocated
     int64_t tape_cap = 0;    // records per chain of the last run
     // plan
@@ -111,7 +113,7 @@ void free_ctx(pns_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void *ptrs[] = {c->d_q, c->d_rowptr, c->d_col, c->d_diag, c->d_b, c->d_betas, c->d_inst, c->d_chain,
                     c->d_state, c->d_x, c->d_fields, c->d_cta, c->d_cta_chains, c->d_status, c->d_tape_flip,
-                    c->d_tape_m,  c->d_tape_x, c->d_tape_E, c->d_xbest};
+                    c->d_tape_m,  c->d_tape_x, c->d_tape_E, c->d_xbest, c->d_wtab, c->d_wtab_desc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -437,7 +439,9 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
     if (m.spec > 0 && !spec_allowed(c)) m.spec = 0;
     if (cfg->track_best) m.spec = 0;  // X_max is kept by the per-flip kernel
     if (m.spec > 0) m.prod = 0;
-    m.sweep = 0;
+    // The set sweep (systematic sets) evaluates each set once per state
+    // instead of once per record.
+    m.sweep = m.spec == 8 ? 1 : 0;
     if (const char *e = getenv("PNS_SWEEP")) m.sweep = atoi(e) ? 1 : 0;
     if (m.sweep && !(m.spec > 0 && sweep_allowed(c, m.spec))) m.sweep = 0;
     // Period blocking takes the dependent row loads off the record chain of
@@ -588,6 +592,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         add(Mapping{8, 0, 0, c->per_cta});
         for (int d : {4, 8, 16}) add(Mapping{1, 0, d, c->per_cta});
         add(Mapping{1, 0, 8, c->per_cta, 0, 0, 1});
+        if (c->per_cta == 0) add(Mapping{1, 0, 8, 1, 0, 0, 1});  // one chain per CTA: two CTAs share an SM
         for (int gw : {0, c->R, (c->R + 1) / 2, (c->R + 3) / 4}) add(Mapping{1, 0, 0, c->per_cta, 1, gw});
     } else {
         for (int T : Ts_csr) add(Mapping{T, 0, 0, c->per_cta});
@@ -937,6 +942,52 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     CU(cudaMemcpyAsync(c->d_state, cs.data(), sizeof(ChainState) * cs.size(), cudaMemcpyHostToDevice, s));
     CU(launch_init_fields(c->fmt, c->qtype, c->hbytes, c->d_inst, c->d_chain, c->d_x, c->d_fields, c->d_state,
                           c->chains, c->W, c->LD, c->max_ld, s));
+    // ---- weight tables: integer dense Q, Unbiased PNS, fixed temperatures --------
+    if (!c->is_float && c->fmt == PNS_DENSE && cfg->variant == PNS_UNBIASED && cfg->swap_interval == 0) {
+        std::vector<std::pair<uint32_t, int2>> seen;  // beta bits -> (first entry, entries)
+        std::vector<int2> desc(c->chains);
+        int64_t total = 0;
+        std::vector<std::vector<float>> betas(n_probs);
+        for (int p = 0; p < n_probs; ++p) {
+            betas[p].resize(c->inst[p].R);
+            CU(cudaMemcpy(betas[p].data(), c->d_betas + c->inst[p].beta_off, sizeof(float) * c->inst[p].R,
+                          cudaMemcpyDeviceToHost));
+        }
+        for (int64_t i = 0; i < c->chains; ++i) {
+            const float beta = betas[chains[i].inst][chains[i].slot];
+            uint32_t bits;
+            memcpy(&bits, &beta, sizeof(bits));
+            int2 d = make_int2(0, 0);
+            bool found = false;
+            for (const auto &e : seen)
+                if (e.first == bits) {
+                    d = e.second;
+                    found = true;
+                    break;
+                }
+            if (!found) {
+                const int32_t ent = wtab_entries(beta);
+                if (ent > 0 && total + ent < (1ll << 30)) {
+                    d = make_int2(static_cast<int32_t>(total), ent);
+                    total += ent;
+                }
+                seen.push_back({bits, d});
+            }
+            desc[i] = d;
+        }
+        if (total > 0) {
+            CU(cudaMalloc(&c->d_wtab, sizeof(float4) * total));
+            CU(cudaMalloc(&c->d_wtab_desc, sizeof(int2) * c->chains));
+            CU(cudaMemcpyAsync(c->d_wtab_desc, desc.data(), sizeof(int2) * c->chains, cudaMemcpyHostToDevice, s));
+            for (const auto &e : seen)
+                if (e.second.y > 0) {
+                    float beta;
+                    memcpy(&beta, &e.first, sizeof(beta));
+                    CU(launch_build_wtab(c->d_wtab + e.second.x, beta, e.second.y, s));
+                }
+            CU(cudaStreamSynchronize(s));  // (desc is a host vector)
+        }
+    }
     if (cfg->track_best) {
         // X_max starts as the initial state (Algorithms 8-10)
         CU(cudaMalloc(&c->d_xbest, sizeof(uint32_t) * c->W * c->chains));
@@ -1024,6 +1075,8 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.prod = c->prod;
     // speculative row loads for Unbiased PNS when Q does not stay in L2
     P.gw = c->gw;
+    P.wtab = c->d_wtab;
+    P.wtab_desc = c->d_wtab_desc;
     P.prefetch = (c->cfg.variant == PNS_UNBIASED && c->q_bytes > (64ull << 20)) ? 1 : 0;
     if (const char *e = getenv("PNS_PREFETCH")) P.prefetch = atoi(e) ? 1 : 0;
     P.chain_base = static_cast<uint32_t>(c->cfg.chain_base);

@@ -89,6 +89,8 @@ struct KParams {
     uint32_t group_base;    // global id of exchange group 0
     int32_t prefetch;       // Unbiased: start the winner's row load before the budget test
     int32_t gw;             // period-blocked kernel: warps per exchange group
+    const float4 *wtab;     // integer Q: weight tables e^{-beta d}, d = 0, 1, ... (w, its two quantised parts)
+    const int2 *wtab_desc;  // per chain: (first entry, entries); entries 0 = no table
 };
 
 PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }

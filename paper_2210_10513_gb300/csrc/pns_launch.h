@@ -52,6 +52,11 @@ bool sweep_supported(int qtype, int D, int n, int k);
 cudaError_t launch_sweep(int qtype, int max_sets, const KParams &P, int grid, int block, size_t smem,
                          cudaStream_t s);
 int32_t sweep_chain_bytes(int32_t ld, int32_t n, int32_t k, int32_t hbytes, int32_t D);
+// Weight table of an integer QUBO at inverse temperature beta: entry d holds
+// w = e^{-beta d} as the samplers compute it and w's two 16-bit quantised
+// parts; entries at and past `entries` are all zero.
+int32_t wtab_entries(float beta);
+cudaError_t launch_build_wtab(float4 *tab, float beta, int32_t entries, cudaStream_t s);
 
 // Period-blocked kernel for Unbiased PNS with systematic sets and replica
 // exchange on dense Q (k <= 128): one warp per chain, the group's set

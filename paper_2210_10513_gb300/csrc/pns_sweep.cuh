@@ -107,6 +107,18 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     int64_t tape_pos = 0;
     int64_t sum_int = 0;  // sum of this launch's multiplicities (exact integers <= L0)
     int64_t done = 0;
+    // integer Q: the weights e^{-beta d} and their quantised parts come from
+    // the chain's table (entry d for the integer d = delta+ - anchor; the last
+    // entry and everything past it are zero)
+    int32_t wt_n = 0;
+    const float4 *wtab = nullptr;
+    if constexpr (!std::is_same<HT, float>::value) {
+        if (P.wtab_desc) {
+            const int2 td = P.wtab_desc[cid];
+            wt_n = td.y;
+            wtab = P.wtab + td.x;
+        }
+    }
     sync_team();
 
     auto delta_of = [&](int i) -> D_t {
@@ -152,22 +164,48 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
             for (int u = 0; u < SPW; ++u) {
                 sa[u] = 0u;
                 sb[u] = 0u;
+            }
+            bool tabled = false;
+            if constexpr (!std::is_same<HT, float>::value) {
+                if (wt_n > 0) {  // (the same for the whole chain)
+                    tabled = true;
 #pragma unroll
-                for (int v = 0; v < CPT; ++v) {
-                    const int t = t0 + v;
-                    if (v < cpl && t < k) {
-                        const float wv = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u][v]), amin[u])));
-                        const float ws = __fmul_rn(wv, 65536.0f);
-                        const float wa = truncf(ws);
-                        sa[u] += __float2uint_rz(wa);
-                        sb[u] += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                        if (own[u]) wts[sg[u] * L.kpad + t] = wv;
+                    for (int u = 0; u < SPW; ++u) {
+#pragma unroll
+                        for (int v = 0; v < CPT; ++v) {
+                            const int t = t0 + v;
+                            if (v < cpl && t < k) {
+                                const int32_t d = A::pos(dl[u][v]) - amin[u];
+                                const float4 e = __ldg(wtab + (d < wt_n ? d : wt_n - 1));
+                                sa[u] += __float_as_uint(e.y);
+                                sb[u] += __float_as_uint(e.z);
+                                if (own[u]) wts[sg[u] * L.kpad + t] = e.x;
+                            }
+                        }
+                    }
+                }
+            }
+            if (!tabled) {
+#pragma unroll
+                for (int u = 0; u < SPW; ++u) {
+#pragma unroll
+                    for (int v = 0; v < CPT; ++v) {
+                        const int t = t0 + v;
+                        if (v < cpl && t < k) {
+                            const float wv = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u][v]), amin[u])));
+                            const float ws = __fmul_rn(wv, 65536.0f);
+                            const float wa = truncf(ws);
+                            sa[u] += __float2uint_rz(wa);
+                            sb[u] += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
+                            if (own[u]) wts[sg[u] * L.kpad + t] = wv;
+                        }
                     }
                 }
             }
             // the per-set scalars, lane u for set u: anchor e^{-beta A},
             // p and -ln(1 - p)
             float af = 0.0f;
+            int32_t ai = 0;
             uint64_t S = 0;
             int my_sg = 0;
             bool my_own = false;
@@ -177,12 +215,15 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb[u]);
                 if (lane == u) {
                     af = A::tof(amin[u]);
+                    if constexpr (!std::is_same<HT, float>::value) ai = amin[u];
                     S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
                     my_sg = sg[u];
                     my_own = own[u];
                 }
             }
-            const float anchor_e = det_expf(-__fmul_rn(beta, af));
+            float anchor_e;
+            if (tabled) anchor_e = __ldg(wtab + (ai < wt_n ? ai : wt_n - 1)).x;
+            else anchor_e = det_expf(-__fmul_rn(beta, af));
             const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
             const float p = mult_p(S, k, anchor_f);
             const float c = det_neg_log1m(p);  // (used only when 0 < p < 1)

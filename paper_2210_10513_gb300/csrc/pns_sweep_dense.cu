@@ -45,6 +45,35 @@ cudaError_t launch_sweep(int qtype, int max_sets, const KParams &P, int grid, in
     }
 }
 
+// Entries of the table: up to the first d with beta d > 87 in fp32 (where the
+// deterministic exponential returns 0 for every larger d as well), plus two
+// zero entries; 0 (no table) past 8192 entries.
+int32_t wtab_entries(float beta) {
+    if (!(beta > 0.0f)) return 0;
+    for (int32_t d = 0; d <= 8190; ++d) {
+        const float prod = beta * static_cast<float>(d);  // (IEEE fp32 product, as on the device)
+        if (!(-prod >= -87.0f)) return d + 2;
+    }
+    return 0;
+}
+
+__global__ void build_wtab_kernel(float4 *tab, float beta, int32_t entries) {
+    for (int32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < entries; d += gridDim.x * blockDim.x) {
+        const float w = det_expf(-__fmul_rn(beta, __int2float_rn(d)));
+        const float ws = __fmul_rn(w, 65536.0f);
+        const float wa = truncf(ws);
+        const uint32_t a = __float2uint_rz(wa);
+        const uint32_t b = __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
+        tab[d] = make_float4(w, __uint_as_float(a), __uint_as_float(b), 0.0f);
+    }
+}
+
+cudaError_t launch_build_wtab(float4 *tab, float beta, int32_t entries, cudaStream_t s) {
+    if (entries <= 0) return cudaSuccess;
+    build_wtab_kernel<<<(entries + 255) / 256, 256, 0, s>>>(tab, beta, entries);
+    return cudaGetLastError();
+}
+
 int32_t sweep_chain_bytes(int32_t ld, int32_t n, int32_t k, int32_t hbytes, int32_t D) {
     (void)D;
     return sweep_smem(ld, hbytes, k, sweep_sets(n, k)).total;

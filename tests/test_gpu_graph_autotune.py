@@ -86,7 +86,7 @@ def test_autotuned_mapping_equals_heuristic(tmp_path, monkeypatch, variant):
     assert cache.exists() and len(cache.read_text().strip().splitlines()) == 1
     # a second context takes the cached choice
     s2 = _sampler(autotune=True, variant=variant)
-    for key in ("team_warps", "producer_warps", "spec_depth", "ctas"):
+    for key in ("team_warps", "producer_warps", "spec_depth", "set_sweep", "ctas"):
         assert getattr(s2.info, key) == getattr(info, key)
     got2 = _runs(s2, [700])[0]
     _equal(got2, ref)

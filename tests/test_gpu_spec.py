@@ -20,6 +20,7 @@ def _problem(n, lo, hi, seed, dtype, beta):
                                               ("metropolis", 1, "systematic")])
 def test_spec_matches_oracle(monkeypatch, depth, variant, k, subset):
     monkeypatch.setenv("PNS_SPEC_DEPTH", depth)
+    monkeypatch.setenv("PNS_SWEEP", "0")  # (the set sweep has its own tests)
     p = _problem(1024, -100, 100, 7, np.int16, 0.05)
     cfg = dict(variant=variant, k=k, subset=subset, chains_per_replica=4, seed=13, L0=100)
     g = gpu_run([p], 3000, tape=True, **cfg)
@@ -34,6 +35,7 @@ def test_spec_equals_sequential_kernel(monkeypatch, beta):
     p = dict(n=200, q=synth.dense_normal(200, 1.0, 4), b=synth.vector_normal(200, 1.0, 4), betas=[beta, 2 * beta])
     cfg = dict(variant="unbiased", k=13, chains_per_replica=5, seed=2, L0=50)
     monkeypatch.setenv("PNS_SPEC_DEPTH", "0")
+    monkeypatch.setenv("PNS_SWEEP", "0")
     a = gpu_run([p], 2500, runs=2, tape=True, **cfg)
     monkeypatch.setenv("PNS_SPEC_DEPTH", "8")
     b = gpu_run([p], 2500, runs=2, tape=True, **cfg)

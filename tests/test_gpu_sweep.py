@@ -21,9 +21,11 @@ def _sweep(monkeypatch):
 
 
 @pytest.mark.parametrize("k", [128, 64, 32])
-@pytest.mark.parametrize("beta", [0.05, 0.5])
+@pytest.mark.parametrize("beta", [0.05, 0.5, 0.005])
 def test_sweep_matches_oracle_int16(monkeypatch, k, beta):
-    # n = 1024: 8, 16 or 32 sets, so 1, 2 or 4 per warp
+    # n = 1024: 8, 16 or 32 sets, so 1, 2 or 4 per warp; the weights come
+    # from the tabled e^{-beta d} at beta 0.05 and 0.5 (1742 and 176 entries)
+    # and from the exponential itself at beta 0.005 (over 8192 entries)
     _sweep(monkeypatch)
     p = _problem(1024, -100, 100, 7, np.int16, beta)
     cfg = dict(variant="unbiased", k=k, chains_per_replica=4, seed=13, L0=100)

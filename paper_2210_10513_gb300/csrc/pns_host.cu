@@ -444,6 +444,9 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
     m.sweep = m.spec == 8 ? 1 : 0;
     if (const char *e = getenv("PNS_SWEEP")) m.sweep = atoi(e) ? 1 : 0;
     if (m.sweep && !(m.spec > 0 && sweep_allowed(c, m.spec))) m.sweep = 0;
+    // one chain per CTA when two CTAs per SM hold them all: the deciding
+    // warps of different chains then rarely share an SM
+    if (m.sweep && m.per_cta == 0 && c.chains <= 2ll * c.num_sms) m.per_cta = 1;
     // Period blocking takes the dependent row loads off the record chain of
     // every exchange group (whose hottest replica sets the pace).
     m.block = block_allowed(c) && cfg->warps_per_chain <= 1 && !cfg->track_best ? 1 : 0;

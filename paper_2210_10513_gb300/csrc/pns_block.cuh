@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
                     const float wa = truncf(ws);
                     sa += __float2uint_rz(wa);
                     sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                    const uint32_t kb = __float_as_uint(__fdiv_rn(ex[u], w));
+                    const uint32_t kb = __float_as_uint(race_key(ex[u], w));
                     if (kb < bkey) {  // t ascending: the first minimum is kept
                         bkey = kb;
                         bpos = static_cast<uint32_t>(t);

@@ -119,6 +119,12 @@ __device__ __forceinline__ void add_chunk(HT *h, const uint4 &v, bool up) {
 // Philox word t of (RACE, chain, step).
 __device__ __forceinline__ float race_exp(uint32_t word) { return det_neg_log1m(u01_fine(word)); }
 
+// Race key E / w (Proposition 5).  Exact for every normal w; for w = 0,
+// subnormal w or a key past the fp32 range the result is +inf or NaN, whose
+// bits exceed every finite key, as IEEE's +inf or huge quotient does there:
+// the least key, the anchor's E <= 16.7, is unchanged.
+__device__ __forceinline__ float race_key(float e, float w) { return div_rn_pos(e, w); }
+
 // Scalars of one record that do not depend on the chain state.
 struct RecordDraws {
     float e1;      // Exp(1) of the multiplicity, from STEP words 0 and 1
@@ -205,7 +211,7 @@ __device__ __forceinline__ float u64_to_f32_rn(uint64_t v) {
 // 1 + Geom(p).  anchor_f = e^{-beta A} (1 when A = 0).
 __device__ __forceinline__ float mult_p(uint64_t S, int32_t k, float anchor_f) {
     float ps = __fmul_rn(u64_to_f32_rn(S), 0x1p-32f);
-    ps = __fdiv_rn(ps, __int2float_rn(k));
+    ps = div_rn_pos(ps, __int2float_rn(k));  // (ps >= 1: the anchor's weight is 1)
     return __fmul_rn(ps, anchor_f);
 }
 
@@ -224,7 +230,9 @@ __device__ __forceinline__ Mult mult_from(float p, float c, float e1) {
         r.fgl = __int_as_float(0x7f800000);
         return r;
     }
-    const float g = __fdiv_rn(e1, c);
+    // (c normal: exact wherever g < 2^63; c subnormal or g past the fp32 range:
+    // a quotient at or above 2^63 or NaN, saturated below, as IEEE's would be)
+    const float g = div_rn_pos(e1, c);
     if (!(g < 0x1p63f)) {
         r.sat = 1;
         r.mi = -1;
@@ -637,7 +645,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                 const float wa = truncf(ws);
                 sa += __float2uint_rz(wa);
                 sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                const uint32_t kb = __float_as_uint(__fdiv_rn(ex_of(t, step), w));
+                const uint32_t kb = __float_as_uint(race_key(ex_of(t, step), w));
                 if (kb < bkey) {  // t ascending per thread: the first minimum is kept
                     bkey = kb;
                     bpos = static_cast<uint32_t>(t);

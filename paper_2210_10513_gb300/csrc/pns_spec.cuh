@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                 if (fits) {  // (uniform across the warp)
                     uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu;
                     auto race = [&](int t, float wv, uint32_t word) {
-                        const uint32_t kb = __float_as_uint(__fdiv_rn(race_exp(word), wv));
+                        const uint32_t kb = __float_as_uint(race_key(race_exp(word), wv));
                         if (kb < bkey) {  // t ascending per lane: the first minimum is kept
                             bkey = kb;
                             bpos = static_cast<uint32_t>(t);

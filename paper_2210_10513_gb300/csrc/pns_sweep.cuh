@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                                 cur_b = bt;
                             }
                             const float ex = race_exp(pick_word(blk, static_cast<uint32_t>(t) & 3u));
-                            const uint32_t kb = __float_as_uint(__fdiv_rn(ex, wv[t]));
+                            const uint32_t kb = __float_as_uint(race_key(ex, wv[t]));
                             if (kb < bkey) {  // t ascending per lane: the first minimum is kept
                                 bkey = kb;
                                 bpos = static_cast<uint32_t>(t);

@@ -3,7 +3,11 @@
 //  - div_log_range(m - 1, m + 1) equals IEEE division (__fdiv_rn) for every
 //    m that det_logf produces (all 2^23 mantissas, both halves of the range);
 //  - det_expf (shifter rounding, selects) equals the form with rintf and an
-//    early return, for every float y in [-88, 0] and a sweep outside it.
+//    early return, for every float y in [-88, 0] and a sweep outside it;
+//  - div_rn_pos equals __fdiv_rn on the samplers' division ranges: every
+//    normal divisor of the range with 24 dividends spread over theirs (race
+//    keys E / w, multiplicity E1 / -ln(1 - p)), and S 2^-32 / k for every
+//    k <= 128 with every 5th dividend.
 // Prints "mismatches <count>" and exits 0 when the program itself ran.
 #include <cstdio>
 #include <cstdint>
@@ -58,14 +62,78 @@ __global__ void check_exp(unsigned long long *bad) {
     atomicAdd(bad, nb);
 }
 
+__device__ float spread(int i, int n, int elo, int ehi, uint32_t salt) {
+    // dividend i of n: exponent stepped over [elo, ehi), hashed mantissa
+    uint32_t h = (static_cast<uint32_t>(i) + 1u) * 2654435761u ^ salt;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const int e = elo + (ehi - elo) * i / n;
+    return __uint_as_float((static_cast<uint32_t>(e + 127) << 23) | (h & 0x007FFFFFu));
+}
+
+// every divisor with exponent in [eblo, ebhi) against NA dividends in
+// [2^ealo, 2^eahi); compared where the IEEE quotient is below `cap`, and
+// elsewhere the fast quotient must not fall below cap either (NaN counts as
+// not below)
+__global__ void check_div_pos(int eblo, int ebhi, int ealo, int eahi, float cap, unsigned long long *bad,
+                              unsigned long long *count) {
+    constexpr int NA = 24;
+    unsigned long long nb = 0, nc = 0;
+    const uint32_t total = static_cast<uint32_t>(ebhi - eblo) << 23;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = eblo + static_cast<int>(idx >> 23);
+        const float y = __uint_as_float((static_cast<uint32_t>(e + 127) << 23) | (idx & 0x007FFFFFu));
+        for (int i = 0; i < NA; ++i) {
+            const float x = spread(i, NA, ealo, eahi, 0x9E3779B9u);
+            const float ref = __fdiv_rn(x, y);
+            const float got = div_rn_pos(x, y);
+            if (ref < cap) {
+                nc++;
+                if (__float_as_uint(got) != __float_as_uint(ref)) nb++;
+            } else if (got < cap) {
+                nb++;
+            }
+        }
+    }
+    atomicAdd(bad, nb);
+    atomicAdd(count, nc);
+}
+
+// S 2^-32 / k: every k in 1..128, every 5th float in [2^-32, 2^8)
+__global__ void check_div_k(unsigned long long *bad, unsigned long long *count) {
+    unsigned long long nb = 0, nc = 0;
+    const uint32_t lo = 0x2F800000u, hi = 0x43800000u;  // 2^-32, 2^8
+    for (uint32_t u = lo + 5u * (blockIdx.x * blockDim.x + threadIdx.x); u < hi; u += 5u * gridDim.x * blockDim.x) {
+        const float x = __uint_as_float(u);
+        for (int k = 1; k <= 128; ++k) {
+            const float y = __int2float_rn(k);
+            nc++;
+            if (__float_as_uint(div_rn_pos(x, y)) != __float_as_uint(__fdiv_rn(x, y))) nb++;
+        }
+    }
+    atomicAdd(bad, nb);
+    atomicAdd(count, nc);
+}
+
 int main() {
-    unsigned long long *d, h[2] = {0, 0};
-    if (cudaMalloc(&d, 16) != cudaSuccess) return 2;
-    cudaMemset(d, 0, 16);
+    unsigned long long *d, h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (cudaMalloc(&d, 64) != cudaSuccess) return 2;
+    cudaMemset(d, 0, 64);
     check_div<<<608, 256>>>(d);
     check_exp<<<1216, 256>>>(d + 1);
+    // race keys: E in [2^-56, 2^5), every normal w in [2^-126, 2); keys at or
+    // above 3e38 (never the least: the anchor's key is E <= 16.7) need only stay there
+    check_div_pos<<<1216, 256>>>(-126, 1, -56, 5, 3.0e38f, d + 2, d + 3);
+    // multiplicity: E1 in [2^-25, 2^6), every normal -ln(1 - p) in [2^-126, 2^6);
+    // exact below 2^63 (the saturation bound), at or above it elsewhere
+    check_div_pos<<<1216, 256>>>(-126, 6, -25, 6, 0x1p63f, d + 4, d + 5);
+    check_div_k<<<1216, 256>>>(d + 6, d + 7);
     if (cudaDeviceSynchronize() != cudaSuccess) return 3;
-    cudaMemcpy(h, d, 16, cudaMemcpyDeviceToHost);
+    cudaMemcpy(h, d, 64, cudaMemcpyDeviceToHost);
     printf("div_mismatches %llu\nexp_mismatches %llu\n", h[0], h[1]);
+    printf("race_div_mismatches %llu\nrace_div_compared %llu\n", h[2], h[3]);
+    printf("mult_div_mismatches %llu\nmult_div_compared %llu\n", h[4], h[5]);
+    printf("k_div_mismatches %llu\nk_div_compared %llu\n", h[6], h[7]);
     return 0;
 }

@@ -24,3 +24,6 @@ def test_detmath_exhaustive(tmp_path):
     vals = dict(line.split() for line in out.strip().splitlines())
     assert int(vals["div_mismatches"]) == 0
     assert int(vals["exp_mismatches"]) == 0
+    for name in ("race", "mult", "k"):
+        assert int(vals[name + "_div_compared"]) > 10 ** 9
+        assert int(vals[name + "_div_mismatches"]) == 0, name

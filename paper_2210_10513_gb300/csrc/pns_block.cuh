@@ -307,48 +307,49 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
                 }
             }
             const int t0 = 4 * lane;
+            // branch-free over the lane's four positions: positions at or
+            // past k read position k - 1 (in bounds) and are masked out
+            const int tb = t0 < k ? t0 : ((k - 1) & ~3);  // (a 16-byte aligned block inside the set)
+            HT hv[4];
+            CT bv[4], dv[4];
+            *reinterpret_cast<uint4 *>(hv) = *reinterpret_cast<const uint4 *>(insf + tb);
+            *reinterpret_cast<uint4 *>(bv) = *reinterpret_cast<const uint4 *>(sub_b + tb);
+            *reinterpret_cast<uint4 *>(dv) = *reinterpret_cast<const uint4 *>(sub_d + tb);
             D dl[4];
+            bool in_set[4];
             uint32_t lmin = 0xFFFFFFFFu;
-            if (t0 < k) {
-                // the lane's four positions are contiguous: one 16-byte read per array
-                HT hv[4];
-                CT bv[4], dv[4];
-                *reinterpret_cast<uint4 *>(hv) = *reinterpret_cast<const uint4 *>(insf + t0);
-                *reinterpret_cast<uint4 *>(bv) = *reinterpret_cast<const uint4 *>(sub_b + t0);
-                *reinterpret_cast<uint4 *>(dv) = *reinterpret_cast<const uint4 *>(sub_d + t0);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int t = t0 + u;
-                    if (t < k) {
-                        const int i = bit_of(t);
-                        const bool xi = (xw[i >> 5] >> (i & 31)) & 1u;
-                        dl[u] = A::delta(hv[u], bv[u], dv[u], xi);
-                        const uint32_t kd = A::key(A::pos(dl[u]));
-                        lmin = kd < lmin ? kd : lmin;
-                    }
-                }
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u;
+                in_set[u] = t < k;
+                int i = s0 + (in_set[u] ? t : 0);
+                i = i >= n ? i - n : i;
+                const bool xi = (xw[i >> 5] >> (i & 31)) & 1u;
+                dl[u] = A::delta(hv[u], bv[u], dv[u], xi);
+                const uint32_t kd = A::key(A::pos(dl[u]));
+                lmin = in_set[u] && kd < lmin ? kd : lmin;
             }
-            const D amin = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin));
-            const float af = A::tof(amin);
-            const float anchor_f = af > 0.0f ? det_expf(-__fmul_rn(beta, af)) : 1.0f;
             float exn[4], e1n;
             draws(step + 1, exn, e1n);
+            const D amin = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin));
+            const float af = A::tof(amin);
+            const float anchor_e = det_expf(-__fmul_rn(beta, af));
+            const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
             uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int t = t0 + u;
-                if (t < k) {
-                    const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u]), amin)));
-                    const float ws = __fmul_rn(w, 65536.0f);
-                    const float wa = truncf(ws);
-                    sa += __float2uint_rz(wa);
-                    sb += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                    const uint32_t kb = __float_as_uint(race_key(ex[u], w));
-                    if (kb < bkey) {  // t ascending: the first minimum is kept
-                        bkey = kb;
-                        bpos = static_cast<uint32_t>(t);
-                    }
-                }
+                const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u]), amin)));
+                const float ws = __fmul_rn(w, 65536.0f);
+                const float wa = truncf(ws);
+                const uint32_t qa = __float2uint_rz(wa);
+                const uint32_t qb = __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
+                sa += in_set[u] ? qa : 0u;
+                sb += in_set[u] ? qb : 0u;
+                const uint32_t kb = in_set[u] ? __float_as_uint(race_key(ex[u], w)) : 0xFFFFFFFFu;
+                const bool better = kb < bkey;  // t ascending: the first minimum is kept
+                bkey = better ? kb : bkey;
+                bpos = better ? static_cast<uint32_t>(t) : bpos;
             }
             const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
             const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);

@@ -179,30 +179,19 @@ __device__ __forceinline__ bool mult_fits(const Mult &mu, int64_t L) {
 
 // Round-to-nearest-even conversion of an unsigned 64-bit integer to fp32 with
 // 32-bit integer operations only (GB300 runs 64-bit int<->float conversions on
-// its slow fp64 pipe).  Equal to __ull2float_rn for every input.
+// its slow fp64 pipe), branch-free: v is normalised so that its leading one
+// sits at bit 63, the top 24 bits are kept and rounded by the 40 dropped ones
+// (half way: to even), and the result is scaled back by an exact power of 2.
+// Equal to __ull2float_rn for every input.
 __device__ __forceinline__ float u64_to_f32_rn(uint64_t v) {
-    const uint32_t hi = static_cast<uint32_t>(v >> 32);
-    const uint32_t lo = static_cast<uint32_t>(v);
-    if (hi == 0u && lo < (1u << 24)) return __uint2float_rn(lo);  // exact
-    const int bits = hi ? 64 - __clz(static_cast<int>(hi)) : 32 - __clz(static_cast<int>(lo));
-    const int sh = bits - 24;  // bits dropped, 1..40
-    uint32_t m;
-    bool round_up;
-    if (sh < 32) {
-        m = static_cast<uint32_t>(v >> sh);
-        const uint32_t rem = static_cast<uint32_t>(v) & ((1u << sh) - 1u);
-        const uint32_t half = 1u << (sh - 1);
-        round_up = rem > half || (rem == half && (m & 1u));
-    } else {
-        m = hi >> (sh - 32);
-        const uint32_t remh = hi & ((1u << (sh - 32)) - 1u);  // bits of hi below m
-        const uint32_t halfh = sh == 32 ? 0u : 1u << (sh - 33);
-        // the dropped part is remh * 2^32 + lo; half is 2^(sh-1)
-        if (sh == 32) round_up = lo > 0x80000000u || (lo == 0x80000000u && (m & 1u));
-        else round_up = remh > halfh || (remh == halfh && (lo > 0u || (m & 1u)));
-    }
-    if (round_up) m += 1u;  // m <= 2^24, exact in fp32
-    return __fmul_rn(__uint2float_rn(m), pow2f(sh));
+    const int z = __clzll(static_cast<long long>(v)) & 63;  // (v = 0 takes the select below)
+    const uint64_t nv = v << z;
+    const uint32_t top = static_cast<uint32_t>(nv >> 40);
+    const uint64_t rest = nv << 24;  // the dropped bits, at the top
+    const bool up = rest > 0x8000000000000000ull || (rest == 0x8000000000000000ull && (top & 1u));
+    const uint32_t m = top + (up ? 1u : 0u);  // <= 2^24, exact in fp32
+    const float r = __fmul_rn(__uint2float_rn(m), pow2f(40 - z));
+    return v == 0ull ? 0.0f : r;
 }
 
 // The multiplicity splits into a part fixed by the state and the set (the
@@ -215,44 +204,29 @@ __device__ __forceinline__ float mult_p(uint64_t S, int32_t k, float anchor_f) {
     return __fmul_rn(ps, anchor_f);
 }
 
-// M from p, c = -ln(1 - p) (read only when 0 < p < 1) and e1.
+// M from p, c = -ln(1 - p) (read only when 0 < p < 1) and e1: p >= 1 gives
+// M = 1, p <= 0 saturates, else g = e1 / c saturates at 2^63 (NaN included)
+// and M = floor(g) + 1.  Branch-free: every case is evaluated and selected.
+// (c normal: g exact wherever g < 2^63; c subnormal or g past the fp32 range:
+// a quotient at or above 2^63 or NaN, saturated, as IEEE's would be.)
 __device__ __forceinline__ Mult mult_from(float p, float c, float e1) {
-    Mult r;
-    r.sat = 0;
-    r.fgl = 0.0f;
-    if (p >= 1.0f) {
-        r.mi = 1;
-        return r;
-    }
-    if (p <= 0.0f) {
-        r.sat = 1;
-        r.mi = -1;
-        r.fgl = __int_as_float(0x7f800000);
-        return r;
-    }
-    // (c normal: exact wherever g < 2^63; c subnormal or g past the fp32 range:
-    // a quotient at or above 2^63 or NaN, saturated below, as IEEE's would be)
     const float g = div_rn_pos(e1, c);
-    if (!(g < 0x1p63f)) {
-        r.sat = 1;
-        r.mi = -1;
-        r.fgl = __int_as_float(0x7f800000);
-        return r;
-    }
     const float fg = floorf(g);
-    if (fg < 16777216.0f) {
-        r.mi = static_cast<int64_t>(__float2int_rz(fg)) + 1;
-    } else {
-        r.mi = -1;
-        r.fgl = fg;
-    }
+    const bool one = p >= 1.0f;
+    const bool sat = !one && (p <= 0.0f || !(g < 0x1p63f));
+    const bool small = fg < 16777216.0f;  // (false for NaN)
+    Mult r;
+    r.sat = sat ? 1 : 0;
+    const int64_t mi_g = small ? static_cast<int64_t>(__float2int_rz(fg)) + 1 : -1;
+    r.mi = one ? 1 : (sat ? -1 : mi_g);
+    r.fgl = one ? 0.0f : (sat ? __int_as_float(0x7f800000) : (small ? 0.0f : fg));
     return r;
 }
 
 __device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anchor_f, float e1) {
     const float p = mult_p(S, k, anchor_f);
-    if (p >= 1.0f || p <= 0.0f) return mult_from(p, 1.0f, e1);
-    return mult_from(p, det_neg_log1m(p), e1);
+    const float c = det_neg_log1m(p);  // (a value for every p; used only when 0 < p < 1)
+    return mult_from(p, c, e1);
 }
 
 // First k distinct values of v_m = floor(word_m n / 2^32), m = 0, 1, ...,
@@ -637,7 +611,8 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
             // e^{-beta A} for the multiplicity, independent of the visits below
             const float af = A::tof(amin);
-            const float anchor_f = af > 0.0f ? det_expf(-__fmul_rn(beta, af)) : 1.0f;
+            const float anchor_e = det_expf(-__fmul_rn(beta, af));
+            const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
             auto visit = [&](int t, D dv) {
                 const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dv), amin)));
                 // floor(w 2^32) as (floor(w 2^16), next 16 bits), all exact in fp32

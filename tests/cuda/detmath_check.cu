@@ -7,12 +7,15 @@
 //  - div_rn_pos equals __fdiv_rn on the samplers' division ranges: every
 //    normal divisor of the range with 24 dividends spread over theirs (race
 //    keys E / w, multiplicity E1 / -ln(1 - p)), and S 2^-32 / k for every
-//    k <= 128 with every 5th dividend.
+//    k <= 128 with every 5th dividend;
+//  - u64_to_f32_rn equals __ull2float_rn on 2^30 hashed values of every
+//    magnitude and on every rounding case (just below, at and above each
+//    half-way point) of every shift.
 // Prints "mismatches <count>" and exits 0 when the program itself ran.
 #include <cstdio>
 #include <cstdint>
 
-#include "pns_device.cuh"
+#include "pns_sampler.cuh"
 
 using namespace pnsk;
 
@@ -116,10 +119,41 @@ __global__ void check_div_k(unsigned long long *bad, unsigned long long *count) 
     atomicAdd(count, nc);
 }
 
+__device__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+__global__ void check_u64(unsigned long long *bad, unsigned long long *count) {
+    unsigned long long nb = 0, nc = 0;
+    for (uint64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 30); i += gridDim.x * blockDim.x) {
+        const uint64_t v = mix64(i) >> (i & 63);
+        nc++;
+        if (__float_as_uint(u64_to_f32_rn(v)) != __float_as_uint(__ull2float_rn(v))) nb++;
+        // rounding cases: a 24-bit top shifted by s, plus the dropped part at
+        // half - 1, half, half + 1 (and 0)
+        const int sh = 1 + static_cast<int>(i % 40);
+        const uint64_t top = (mix64(i + 0x9e37ull) & 0x7FFFFFull) | 0x800000ull;
+        const uint64_t half = 1ull << (sh - 1);
+        const uint64_t base = top << sh;
+        const uint64_t cases[4] = {base, base + half - 1, base + half, base + half + 1};
+        for (int c = 0; c < 4; ++c) {
+            nc++;
+            if (__float_as_uint(u64_to_f32_rn(cases[c])) != __float_as_uint(__ull2float_rn(cases[c]))) nb++;
+        }
+    }
+    atomicAdd(bad, nb);
+    atomicAdd(count, nc);
+}
+
 int main() {
-    unsigned long long *d, h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (cudaMalloc(&d, 64) != cudaSuccess) return 2;
-    cudaMemset(d, 0, 64);
+    unsigned long long *d, h[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (cudaMalloc(&d, 80) != cudaSuccess) return 2;
+    cudaMemset(d, 0, 80);
     check_div<<<608, 256>>>(d);
     check_exp<<<1216, 256>>>(d + 1);
     // race keys: E in [2^-56, 2^5), every normal w in [2^-126, 2); keys at or
@@ -129,11 +163,13 @@ int main() {
     // exact below 2^63 (the saturation bound), at or above it elsewhere
     check_div_pos<<<1216, 256>>>(-126, 6, -25, 6, 0x1p63f, d + 4, d + 5);
     check_div_k<<<1216, 256>>>(d + 6, d + 7);
+    check_u64<<<1216, 256>>>(d + 8, d + 9);
     if (cudaDeviceSynchronize() != cudaSuccess) return 3;
-    cudaMemcpy(h, d, 64, cudaMemcpyDeviceToHost);
+    cudaMemcpy(h, d, 80, cudaMemcpyDeviceToHost);
     printf("div_mismatches %llu\nexp_mismatches %llu\n", h[0], h[1]);
     printf("race_div_mismatches %llu\nrace_div_compared %llu\n", h[2], h[3]);
     printf("mult_div_mismatches %llu\nmult_div_compared %llu\n", h[4], h[5]);
     printf("k_div_mismatches %llu\nk_div_compared %llu\n", h[6], h[7]);
+    printf("u64_mismatches %llu\nu64_compared %llu\n", h[8], h[9]);
     return 0;
 }

@@ -27,3 +27,5 @@ def test_detmath_exhaustive(tmp_path):
     for name in ("race", "mult", "k"):
         assert int(vals[name + "_div_compared"]) > 10 ** 9
         assert int(vals[name + "_div_mismatches"]) == 0, name
+    assert int(vals["u64_compared"]) > 5 * 10 ** 9 and int(vals["u64_mismatches"]) == 0
+    print(vals)

@@ -1087,9 +1087,12 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {
         if (c->blocked) return launch_block(c->qtype, Pl, grid, c->n_threads, c->smem, s);
         if (c->spec > 0 && c->sweep) {
-            int max_sets = 1;
-            for (const InstHost &ih : c->inst) max_sets = std::max(max_sets, sweep_sets(ih.n, ih.k));
-            return launch_sweep(c->qtype, max_sets, Pl, grid, c->n_threads, c->smem, s);
+            int max_sets = 1, max_k = 1;
+            for (const InstHost &ih : c->inst) {
+                max_sets = std::max(max_sets, sweep_sets(ih.n, ih.k));
+                max_k = std::max(max_k, ih.k);
+            }
+            return launch_sweep(c->qtype, max_sets, max_k, Pl, grid, c->n_threads, c->smem, s);
         }
         if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->n_threads, c->smem, s);
         return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->n_threads, c->smem, s);

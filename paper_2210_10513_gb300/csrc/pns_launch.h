@@ -49,7 +49,7 @@ int32_t spec_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, bool list, int32
 // 32), then decide up to 256 records at once.
 int sweep_sets(int n, int k);
 bool sweep_supported(int qtype, int D, int n, int k);
-cudaError_t launch_sweep(int qtype, int max_sets, const KParams &P, int grid, int block, size_t smem,
+cudaError_t launch_sweep(int qtype, int max_sets, int max_k, const KParams &P, int grid, int block, size_t smem,
                          cudaStream_t s);
 int32_t sweep_chain_bytes(int32_t ld, int32_t n, int32_t k, int32_t hbytes, int32_t D);
 // Weight table of an integer QUBO at inverse temperature beta: entry d holds

@@ -51,7 +51,10 @@ PNS_HD int32_t gcd32(int32_t a, int32_t b) {
     return a;
 }
 
-template <typename QT, typename HT, int D, int SPW>
+// CPL: positions per lane, 1, 2 or 4 (k <= 32 CPL); a lane's positions lie in
+// one Philox block of race words.  Positions at or past k are evaluated at
+// position k - 1 and masked, so the loops carry no branches.
+template <typename QT, typename HT, int D, int SPW, int CPL>
 __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(const KParams P) {
     using A = Arith<HT>;
     using D_t = typename A::D;
@@ -102,8 +105,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     const uint64_t seed = P.seed;
     const uint32_t chain_id = static_cast<uint32_t>(cid) + P.chain_base;
     const int r0 = st.set_start % g;
-    const int cpl = (k + 31) >> 5;  // positions per lane (k <= 128)
-    const int t0 = lane * cpl;
+    const int t0 = lane * CPL;
     int64_t tape_pos = 0;
     int64_t sum_int = 0;  // sum of this launch's multiplicities (exact integers <= L0)
     int64_t done = 0;
@@ -139,21 +141,19 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 own[u] = s_ < nsets;
                 sg[u] = own[u] ? s_ : s_ % nsets;
             }
-            D_t dl[SPW][CPT];
+            D_t dl[SPW][CPL];
             uint32_t lmin[SPW];
 #pragma unroll
             for (int u = 0; u < SPW; ++u) {
                 lmin[u] = 0xFFFFFFFFu;
 #pragma unroll
-                for (int v = 0; v < CPT; ++v) {
+                for (int v = 0; v < CPL; ++v) {
                     const int t = t0 + v;
-                    if (v < cpl && t < k) {
-                        int i = sg[u] * g + r0 + t;
-                        i = i >= n ? i - n : i;
-                        dl[u][v] = delta_of(i);
-                        const uint32_t kd = A::key(A::pos(dl[u][v]));
-                        lmin[u] = kd < lmin[u] ? kd : lmin[u];
-                    }
+                    int i = sg[u] * g + r0 + (t < k ? t : k - 1);
+                    i = i >= n ? i - n : i;
+                    dl[u][v] = delta_of(i);
+                    const uint32_t kd = A::key(A::pos(dl[u][v]));
+                    lmin[u] = t < k && kd < lmin[u] ? kd : lmin[u];
                 }
             }
             D_t amin[SPW];
@@ -172,15 +172,13 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
 #pragma unroll
                     for (int u = 0; u < SPW; ++u) {
 #pragma unroll
-                        for (int v = 0; v < CPT; ++v) {
+                        for (int v = 0; v < CPL; ++v) {
                             const int t = t0 + v;
-                            if (v < cpl && t < k) {
-                                const int32_t d = A::pos(dl[u][v]) - amin[u];
-                                const float4 e = __ldg(wtab + (d < wt_n ? d : wt_n - 1));
-                                sa[u] += __float_as_uint(e.y);
-                                sb[u] += __float_as_uint(e.z);
-                                if (own[u]) wts[sg[u] * L.kpad + t] = e.x;
-                            }
+                            const int32_t d = A::pos(dl[u][v]) - amin[u];
+                            const float4 e = __ldg(wtab + (d < wt_n ? d : wt_n - 1));
+                            sa[u] += t < k ? __float_as_uint(e.y) : 0u;
+                            sb[u] += t < k ? __float_as_uint(e.z) : 0u;
+                            if (own[u] && t < k) wts[sg[u] * L.kpad + t] = e.x;
                         }
                     }
                 }
@@ -189,16 +187,14 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
 #pragma unroll
                 for (int u = 0; u < SPW; ++u) {
 #pragma unroll
-                    for (int v = 0; v < CPT; ++v) {
+                    for (int v = 0; v < CPL; ++v) {
                         const int t = t0 + v;
-                        if (v < cpl && t < k) {
-                            const float wv = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u][v]), amin[u])));
-                            const float ws = __fmul_rn(wv, 65536.0f);
-                            const float wa = truncf(ws);
-                            sa[u] += __float2uint_rz(wa);
-                            sb[u] += __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
-                            if (own[u]) wts[sg[u] * L.kpad + t] = wv;
-                        }
+                        const float wv = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u][v]), amin[u])));
+                        const float ws = __fmul_rn(wv, 65536.0f);
+                        const float wa = truncf(ws);
+                        sa[u] += t < k ? __float2uint_rz(wa) : 0u;
+                        sb[u] += t < k ? __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f)) : 0u;
+                        if (own[u] && t < k) wts[sg[u] * L.kpad + t] = wv;
                     }
                 }
             }
@@ -240,17 +236,12 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 const int sig0 = st.set_start / g;
                 int sg = sig0 + (lane * kstep) % nsets;  // set of record lane after lane stays
                 sg = sg >= nsets ? sg - nsets : sg;
-                bool fits = false;
-                Mult mu;
-                mu.mi = 0;
-                mu.sat = 0;
-                mu.fgl = 0.0f;
-                if (lane < nb) {
-                    const float2 pc = table[sg];
-                    const float e1 = record_draws(seed, chain_id, step0 + lane, n, false, true).e1;
-                    mu = mult_from(pc.x, pc.y, e1);
-                    fits = mult_fits_small(mu, static_cast<int32_t>(lane == 0 ? st.L : P.L0));  // (L0 < 2^31)
-                }
+                // (every lane decides; lanes past the last record are masked)
+                const float2 pc = table[sg];
+                const float e1 = record_draws(seed, chain_id, step0 + lane, n, false, true).e1;
+                const Mult mu = mult_from(pc.x, pc.y, e1);
+                const bool fits =
+                    lane < nb && mult_fits_small(mu, static_cast<int32_t>(lane == 0 ? st.L : P.L0));  // (L0 < 2^31)
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fits);
                 moved = bal != 0u;
                 const int first = moved ? __ffs(static_cast<int>(bal)) - 1 : nb;
@@ -271,24 +262,15 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                     const uint64_t step = step0 + first;
                     const float *wv = wts + sf * L.kpad;
                     uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu;
-                    uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t0 >> 2));
-                    uint32_t cur_b = static_cast<uint32_t>(t0 >> 2);
+                    const uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t0 >> 2));
 #pragma unroll
-                    for (int v = 0; v < CPT; ++v) {
+                    for (int v = 0; v < CPL; ++v) {
                         const int t = t0 + v;
-                        if (v < cpl && t < k) {
-                            const uint32_t bt = static_cast<uint32_t>(t) >> 2;
-                            if (bt != cur_b) {
-                                blk = rng_block(seed, TAG_RACE, chain_id, step, bt);
-                                cur_b = bt;
-                            }
-                            const float ex = race_exp(pick_word(blk, static_cast<uint32_t>(t) & 3u));
-                            const uint32_t kb = __float_as_uint(race_key(ex, wv[t]));
-                            if (kb < bkey) {  // t ascending per lane: the first minimum is kept
-                                bkey = kb;
-                                bpos = static_cast<uint32_t>(t);
-                            }
-                        }
+                        const float ex = race_exp(pick_word(blk, static_cast<uint32_t>(t) & 3u));
+                        const uint32_t kb = t < k ? __float_as_uint(race_key(ex, wv[t < k ? t : k - 1])) : 0xFFFFFFFFu;
+                        const bool better = kb < bkey;  // t ascending per lane: the first minimum is kept
+                        bkey = better ? kb : bkey;
+                        bpos = better ? static_cast<uint32_t>(t) : bpos;
                     }
                     const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
                     const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);

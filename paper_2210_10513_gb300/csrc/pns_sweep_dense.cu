@@ -7,21 +7,32 @@ namespace pnsk {
 
 constexpr int SWEEP_WARPS = 8;
 
-template <typename QT, typename HT, int SPW>
+template <typename QT, typename HT, int SPW, int CPL>
 static cudaError_t launch_sweep_t(const KParams &P, int grid, int block, size_t smem, cudaStream_t s) {
-    auto kern = pns_sweep_kernel<QT, HT, SWEEP_WARPS, SPW>;
+    auto kern = pns_sweep_kernel<QT, HT, SWEEP_WARPS, SPW, CPL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<grid, block, smem, s>>>(P);
     return cudaGetLastError();
 }
 
-template <typename QT, typename HT>
+template <typename QT, typename HT, int CPL>
 static cudaError_t sweep_by_spw(int spw, const KParams &P, int grid, int block, size_t smem, cudaStream_t s) {
     switch (spw) {
-    case 1: return launch_sweep_t<QT, HT, 1>(P, grid, block, smem, s);
-    case 2: return launch_sweep_t<QT, HT, 2>(P, grid, block, smem, s);
-    case 4: return launch_sweep_t<QT, HT, 4>(P, grid, block, smem, s);
+    case 1: return launch_sweep_t<QT, HT, 1, CPL>(P, grid, block, smem, s);
+    case 2: return launch_sweep_t<QT, HT, 2, CPL>(P, grid, block, smem, s);
+    case 4: return launch_sweep_t<QT, HT, 4, CPL>(P, grid, block, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename QT, typename HT>
+static cudaError_t sweep_by_cpl(int spw, int cpl, const KParams &P, int grid, int block, size_t smem,
+                                cudaStream_t s) {
+    switch (cpl) {
+    case 1: return sweep_by_spw<QT, HT, 1>(spw, P, grid, block, smem, s);
+    case 2: return sweep_by_spw<QT, HT, 2>(spw, P, grid, block, smem, s);
+    case 4: return sweep_by_spw<QT, HT, 4>(spw, P, grid, block, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -34,13 +45,14 @@ bool sweep_supported(int qtype, int D, int n, int k) {
     return sweep_sets(n, k) <= 4 * SWEEP_WARPS;
 }
 
-cudaError_t launch_sweep(int qtype, int max_sets, const KParams &P, int grid, int block, size_t smem,
+cudaError_t launch_sweep(int qtype, int max_sets, int max_k, const KParams &P, int grid, int block, size_t smem,
                          cudaStream_t s) {
     const int spw = max_sets <= SWEEP_WARPS ? 1 : max_sets <= 2 * SWEEP_WARPS ? 2 : 4;
+    const int cpl = max_k <= 32 ? 1 : max_k <= 64 ? 2 : 4;
     switch (qtype) {
-    case 0: return sweep_by_spw<int16_t, int32_t>(spw, P, grid, block, smem, s);
-    case 1: return sweep_by_spw<int32_t, int32_t>(spw, P, grid, block, smem, s);
-    case 2: return sweep_by_spw<float, float>(spw, P, grid, block, smem, s);
+    case 0: return sweep_by_cpl<int16_t, int32_t>(spw, cpl, P, grid, block, smem, s);
+    case 1: return sweep_by_cpl<int32_t, int32_t>(spw, cpl, P, grid, block, smem, s);
+    case 2: return sweep_by_cpl<float, float>(spw, cpl, P, grid, block, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
         // dependent chain.
         float ex[4], e1;
         auto draws = [&](uint64_t step, float *x, float &e) {
-            const uint4 rw = 4 * lane < k ? rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(lane))
-                                          : make_uint4(0u, 0u, 0u, 0u);
+            // (every lane draws: a lane past the set discards its words, and
+            // the draws stay free of branches)
+            const uint4 rw = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(lane));
             x[0] = race_exp(rw.x);
             x[1] = race_exp(rw.y);
             x[2] = race_exp(rw.z);

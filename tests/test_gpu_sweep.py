@@ -36,6 +36,19 @@ def test_sweep_matches_oracle_int16(monkeypatch, k, beta):
         assert_chain_equal(g, ref[cid], cid, 1024, 3000)
 
 
+@pytest.mark.parametrize("n", [2048, 4096])
+def test_sweep_four_positions_per_lane(monkeypatch, n):
+    # k = 128: 16 or 32 sets (2 or 4 per warp), four positions per lane
+    _sweep(monkeypatch)
+    p = _problem(n, -30, 30, 9, np.int16, 0.05)
+    cfg = dict(variant="unbiased", k=128, chains_per_replica=2, seed=17, L0=100)
+    g = gpu_run([p], 1500, tape=True, **cfg)
+    assert g["info"].set_sweep == 1
+    ref = oracle_run([p], 1500, [0, 1], **cfg)
+    for cid in range(2):
+        assert_chain_equal(g, ref[cid], cid, n, 1500)
+
+
 def test_sweep_sets_not_dividing_n(monkeypatch):
     # n = 96, k = 36: gcd 12, so 8 sets visited 3 apart; odd run lengths end
     # inside a batch of records

@@ -579,19 +579,32 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             }
             if (dead) return true;
             const bool fast = k <= CPT * TCC;
-            // a2 + a3: deltas and the anchor
+            // a2 + a3: deltas and the anchor.  Fast path: NP positions per
+            // thread, one (k <= TCC) or CPT contiguous ones (one Philox block
+            // of race words), evaluated without branches (positions at or
+            // past k read position k - 1 and are masked)
+            // (one position per thread only for one-warp teams: wider teams
+            // serve large k, and the second code path costs them registers)
+            const bool one_pos = TC == 1 && k <= TCC;  // (the same for the whole team)
             D dl[CPT];
             uint32_t lmin = 0xFFFFFFFFu;
-            if (fast) {
+            auto pos_of = [&](auto np_c, int u) {
+                constexpr int NP = decltype(np_c)::value;
+                return NP == 1 ? ctid : CPT * ctid + u;
+            };
+            auto deltas = [&](auto np_c) {
+                constexpr int NP = decltype(np_c)::value;
 #pragma unroll
-                for (int u = 0; u < CPT; ++u) {
-                    const int t = ctid + u * TCC;
-                    if (t < k) {
-                        dl[u] = delta_of(cand(t, sl));
-                        const uint32_t kd = A::key(A::pos(dl[u]));
-                        lmin = kd < lmin ? kd : lmin;
-                    }
+                for (int u = 0; u < NP; ++u) {
+                    const int t = pos_of(np_c, u);
+                    dl[u] = delta_of(cand(t < k ? t : k - 1, sl));
+                    const uint32_t kd = A::key(A::pos(dl[u]));
+                    lmin = t < k && kd < lmin ? kd : lmin;
                 }
+            };
+            if (fast) {
+                if (one_pos) deltas(std::integral_constant<int, 1>{});
+                else deltas(std::integral_constant<int, CPT>{});
             } else {
                 for (int t = ctid; t < k; t += TCC) {
                     const uint32_t kd = A::key(A::pos(delta_of(cand(t, sl))));
@@ -626,12 +639,49 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                     bpos = static_cast<uint32_t>(t);
                 }
             };
-            if (fast) {
+            // race exponentials: from the producer's slot, or from the
+            // thread's one Philox block (position ctid: block ctid / 4; CPT =
+            // 4 positions from 4 ctid: block ctid)
+            static_assert(CPT == 4, "one Philox block per thread");
+            auto weigh = [&](auto np_c) {
+                constexpr int NP = decltype(np_c)::value;
+                float exv[NP];
+                if (prod > 0) {
 #pragma unroll
-                for (int u = 0; u < CPT; ++u) {
-                    const int t = ctid + u * TCC;
-                    if (t < k) visit(t, dl[u]);
+                    for (int u = 0; u < NP; ++u) {
+                        const int t = pos_of(np_c, u);
+                        exv[u] = ex_of(t < k ? t : k - 1, step);
+                    }
+                } else if constexpr (NP == 1) {
+                    const uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(ctid >> 2));
+                    exv[0] = race_exp(pick_word(blk, static_cast<uint32_t>(ctid & 3)));
+                } else {
+                    const uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(ctid));
+                    exv[0] = race_exp(blk.x);
+                    exv[1] = race_exp(blk.y);
+                    exv[2] = race_exp(blk.z);
+                    exv[3] = race_exp(blk.w);
                 }
+#pragma unroll
+                for (int u = 0; u < NP; ++u) {
+                    const int t = pos_of(np_c, u);
+                    const float ex = exv[u];
+                    const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl[u]), amin)));
+                    const float ws = __fmul_rn(w, 65536.0f);
+                    const float wa = truncf(ws);
+                    const uint32_t qa = __float2uint_rz(wa);
+                    const uint32_t qb = __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
+                    sa += t < k ? qa : 0u;
+                    sb += t < k ? qb : 0u;
+                    const uint32_t kb = t < k ? __float_as_uint(race_key(ex, w)) : 0xFFFFFFFFu;
+                    const bool better = kb < bkey;  // t ascending per thread: the first minimum is kept
+                    bkey = better ? kb : bkey;
+                    bpos = better ? static_cast<uint32_t>(t) : bpos;
+                }
+            };
+            if (fast) {
+                if (one_pos) weigh(std::integral_constant<int, 1>{});
+                else weigh(std::integral_constant<int, CPT>{});
             } else {
                 for (int t = ctid; t < k; t += TCC) visit(t, delta_of(cand(t, sl)));
             }

@@ -31,6 +31,8 @@ constexpr int SAMPLES_PER_CTA = 16384;
 constexpr int A_SLAB_BYTES = 128 * 16 * 2;  // 128 rows x 16 bf16
 constexpr int B_SLAB_BYTES = 64 * 16 * 2;   // 64 rows x 16 bf16
 constexpr int STAGE_BYTES = 3 * 4 * A_SLAB_BYTES + 4 * B_SLAB_BYTES;  // 56 KiB
+constexpr int NBUF = 1;               // stage buffers per CTA (two CTAs share an SM and overlap)
+constexpr int MOM_SMEM = NBUF * STAGE_BYTES + 2048;
 constexpr int TMEM_COLS = 256;        // three 64-column fp32 accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int MOM_THREADS = 512;      // 16 warps build the operand tiles
@@ -156,19 +158,19 @@ __global__ void scalar_final_kernel(const double *partials, int blocks, double *
 
 // ---------------------------------------------------------------------------
 // The tensor-core contraction.  512 threads; each CTA takes up to 16384
-// samples in stages of 64, double-buffered: while the tensor cores work on one
-// stage the threads build the next one (the build, not the MMA, sets the pace,
-// so all 16 warps take part in it).
+// samples in stages of 64.  All 16 warps build a stage's operand tiles (the
+// build, not the MMA, sets the pace); with NBUF = 1 stage buffer a CTA needs
+// 58 KiB, so two CTAs share an SM and one builds while the other's MMAs run.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc src, const double *centre, float *partials,
+__global__ void __launch_bounds__(MOM_THREADS, 3 - NBUF) moments_tc_kernel(SampleSrc src, const double *centre, float *partials,
                                                             int32_t *status) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *stage_buf[2] = {sm, sm + STAGE_BYTES};
-    uint16_t *planes = reinterpret_cast<uint16_t *>(sm + 2 * STAGE_BYTES);       // [6][64]
-    uint32_t *bits = reinterpret_cast<uint32_t *>(sm + 2 * STAGE_BYTES + 1024);  // [64][2]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 2 * STAGE_BYTES + 1536);  // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + 2 * STAGE_BYTES + 1552);
-    int32_t *fail = reinterpret_cast<int32_t *>(sm + 2 * STAGE_BYTES + 1556);
+    unsigned char *const stage_base = sm;
+    uint16_t *planes = reinterpret_cast<uint16_t *>(sm + NBUF * STAGE_BYTES);       // [6][64]
+    uint32_t *bits_t = reinterpret_cast<uint32_t *>(sm + NBUF * STAGE_BYTES + 1024);  // [64 rows][2]: bit s = sample s
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + NBUF * STAGE_BYTES + 1536);  // [NBUF]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + NBUF * STAGE_BYTES + 1552);
+    int32_t *fail = reinterpret_cast<int32_t *>(sm + NBUF * STAGE_BYTES + 1556);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -179,8 +181,8 @@ __global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc sr
     const double c = *centre;
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr_of(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr_of(&mbar[1])) : "memory");
+        for (int b = 0; b < NBUF; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr_of(&mbar[b])) : "memory");
         *fail = 0;
     }
     if (warp == 0) {
@@ -213,11 +215,11 @@ __global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc sr
     if (tid < STAGE_K) load_sample(0);
     int committed = 0;  // stages whose MMAs were issued
     for (int g = 0; g < stages; ++g) {
-        const int buf = g & 1;
-        unsigned char *sb = stage_buf[buf];
-        if (g >= 2) {
-            // the MMAs of stage g - 2 read this buffer
-            if (!mbar_wait(saddr_of(&mbar[buf]), static_cast<uint32_t>(((g - 2) >> 1) & 1))) {
+        const int buf = g % NBUF;
+        unsigned char *sb = stage_base + buf * STAGE_BYTES;
+        if (g >= NBUF) {
+            // the MMAs of stage g - NBUF read this buffer
+            if (!mbar_wait(saddr_of(&mbar[buf]), static_cast<uint32_t>(((g - NBUF) / NBUF) & 1))) {
                 if (tid == 0) *fail = 1;
             }
         }
@@ -232,8 +234,30 @@ __global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc sr
                 split3(static_cast<float>(nx_m * (nx_e - c)), pw + 3);
             }
             for (int p = 0; p < 6; ++p) planes[p * STAGE_K + tid] = pw[p];
-            bits[2 * tid] = nx_valid ? nx_x0 : 0u;
-            bits[2 * tid + 1] = nx_valid ? nx_x1 : 0u;
+            // the bits transposed: row i's word w holds bit i of samples
+            // 32 w .. 32 w + 31.  Each warp transposes its two 32 x 32 bit
+            // blocks (lane = sample, bit = row) by the recursive block swap:
+            // at size j, a lane with bit j clear keeps its columns with bit j
+            // clear and takes its partner's (lane + j) same columns moved up
+            // by j; the partner keeps the others and takes the rest moved
+            // down.  Afterwards lane l holds rows l and l + 32.
+            uint32_t r0 = nx_valid ? nx_x0 : 0u, r1 = nx_valid ? nx_x1 : 0u;
+            const int ln = tid & 31;
+#pragma unroll
+            for (int j = 16; j >= 1; j >>= 1) {
+                const uint32_t m = j == 16 ? 0x0000FFFFu
+                                   : j == 8 ? 0x00FF00FFu
+                                   : j == 4 ? 0x0F0F0F0Fu
+                                   : j == 2 ? 0x33333333u
+                                            : 0x55555555u;
+                const uint32_t p0 = __shfl_xor_sync(0xFFFFFFFFu, r0, j);
+                const uint32_t p1 = __shfl_xor_sync(0xFFFFFFFFu, r1, j);
+                const bool low = (ln & j) == 0;
+                r0 = low ? ((r0 & m) | ((p0 & m) << j)) : ((r0 & ~m) | ((p0 & ~m) >> j));
+                r1 = low ? ((r1 & m) | ((p1 & m) << j)) : ((r1 & ~m) | ((p1 & ~m) >> j));
+            }
+            bits_t[2 * ln + (tid >> 5)] = r0;
+            bits_t[2 * (ln + 32) + (tid >> 5)] = r1;
             load_sample(g + 1);
         }
         __syncthreads();
@@ -245,16 +269,17 @@ __global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc sr
             const int o = rem & 7;
             const int i = r & 63;
             const int p = 2 * m + (r >> 6);
+            // samples 8 o .. 8 o + 7: their bits of row i (one byte) mask the
+            // plane's eight weights (one 16-byte read)
+            const uint32_t byte = (bits_t[2 * i + (o >> 2)] >> (8 * (o & 3))) & 0xFFu;
+            const uint4 w8 = *reinterpret_cast<const uint4 *>(planes + p * STAGE_K + 8 * o);
+            const uint32_t wv[4] = {w8.x, w8.y, w8.z, w8.w};
             uint32_t packed[4];
+#pragma unroll
             for (int e2 = 0; e2 < 4; ++e2) {
-                uint32_t lohi = 0u;
-                for (int h = 0; h < 2; ++h) {
-                    const int s = 8 * o + 2 * e2 + h;
-                    const uint32_t word = bits[2 * s + (i >> 5)];
-                    const uint32_t v = ((word >> (i & 31)) & 1u) ? planes[p * STAGE_K + s] : 0u;
-                    lohi |= v << (16 * h);
-                }
-                packed[e2] = lohi;
+                const uint32_t two = byte >> (2 * e2);
+                const uint32_t mask = ((two & 1u) * 0x0000FFFFu) | (((two >> 1) & 1u) * 0xFFFF0000u);
+                packed[e2] = wv[e2] & mask;
             }
             const int slab = o >> 1;
             const int off = m * 4 * A_SLAB_BYTES + slab * A_SLAB_BYTES + (r >> 3) * 256 + (o & 1) * 128 + (r & 7) * 16;
@@ -264,16 +289,13 @@ __global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc sr
         for (int cidx = tid; cidx < 64 * 8; cidx += MOM_THREADS) {
             const int j = cidx >> 3;
             const int o = cidx & 7;
+            const uint32_t byte = (bits_t[2 * j + (o >> 2)] >> (8 * (o & 3))) & 0xFFu;
             uint32_t packed[4];
+#pragma unroll
             for (int e2 = 0; e2 < 4; ++e2) {
-                uint32_t lohi = 0u;
-                for (int h = 0; h < 2; ++h) {
-                    const int s = 8 * o + 2 * e2 + h;
-                    const uint32_t word = bits[2 * s + (j >> 5)];
-                    const uint32_t v = ((word >> (j & 31)) & 1u) ? 0x3F80u : 0u;  // bf16 1.0
-                    lohi |= v << (16 * h);
-                }
-                packed[e2] = lohi;
+                const uint32_t two = byte >> (2 * e2);
+                const uint32_t mask = ((two & 1u) * 0x0000FFFFu) | (((two >> 1) & 1u) * 0xFFFF0000u);
+                packed[e2] = 0x3F803F80u & mask;  // bf16 1.0 where the bit is set
             }
             const int slab = o >> 1;
             const int off = 3 * 4 * A_SLAB_BYTES + slab * B_SLAB_BYTES + (j >> 3) * 256 + (o & 1) * 128 + (j & 7) * 16;
@@ -305,9 +327,9 @@ __global__ void __launch_bounds__(MOM_THREADS, 1) moments_tc_kernel(SampleSrc sr
         committed = g + 1;
     }
     // wait for the MMAs of the last (up to two) committed stages
-    for (int g = committed - 2; g < committed; ++g) {
+    for (int g = committed - NBUF; g < committed; ++g) {
         if (g < 0) continue;
-        if (!mbar_wait(saddr_of(&mbar[g & 1]), static_cast<uint32_t>((g >> 1) & 1))) {
+        if (!mbar_wait(saddr_of(&mbar[g % NBUF]), static_cast<uint32_t>((g / NBUF) & 1))) {
             if (tid == 0) *fail = 1;
         }
     }
@@ -458,7 +480,7 @@ cudaError_t launch_moments(const uint32_t *tape_x, const double *tape_m, const d
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (src.samples > 0) {
-        const int smem = 2 * STAGE_BYTES + 2048;
+        const int smem = MOM_SMEM;
         e = cudaFuncSetAttribute(moments_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         moments_tc_kernel<<<static_cast<unsigned>(ctas), MOM_THREADS, smem, s>>>(src, centre, partials, status);

@@ -479,6 +479,12 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
     int32_t pend_flip = 0;
     double pend_m = 0.0;
     bool pend = false;
+    // Unbiased PNS without exchange: its multiplicities are integers <= L0,
+    // so their sum is kept exactly in int64 and added to the fp64 sum once
+    // at the end (equal to the record-by-record fp64 sum: every partial sum
+    // is an integer below 2^53); the fp64 M is formed only for the tape
+    const bool int_sum = variant == VAR_UNBIASED && !P.pt;
+    int64_t sum_int = 0;
     auto flush_record = [&]() {
         if (pend) {
             if (ctid == 0 && P.tape >= 1 && tape_pos < P.tape_cap) {
@@ -496,6 +502,13 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
         pend_m = m;
         pend = true;
         st.sum_m = __dadd_rn(st.sum_m, m);
+    };
+    auto write_record_int = [&](int32_t flip, int64_t mi) {  // (int_sum)
+        flush_record();
+        pend_flip = flip;
+        pend_m = P.tape >= 1 && ctid == 0 ? static_cast<double>(mi) : 0.0;  // (only the tape reads it)
+        pend = true;
+        sum_int += mi;
     };
 
     // Race exponential of position t in the current record.
@@ -722,18 +735,24 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             if (always_move) prefetch_row(j);
             // a5: multiplicity and budget
             const Mult mu = multiplicity_e1(S, k, anchor_f, rd.e1);
-            double m = mult_md(mu);
             const int sat = mu.sat;
             const D dj = delta_of(j);
             sync_cons();  // reads of h, x and the list are done
             bool move = true;
-            if (variant == VAR_UNBIASED) {
-                const bool fits = mu.mi >= 0 ? mu.mi <= st.L : m <= static_cast<double>(st.L);
+            if (int_sum) {
+                // the budget test in integers (fp64 only for a huge M)
+                const bool fits = mult_fits(mu, st.L);
+                int64_t mrec;
                 if (fits) {
-                    st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(m);
+                    mrec = mu.mi >= 0 ? mu.mi : static_cast<int64_t>(mult_md(mu));
+                    st.L -= mrec;
+                    if (sat) st.saturated += 1;
+                    apply_move(j, always_move);
+                    st.E = __dadd_rn(st.E, A::tod(dj));
+                    st.flips += 1;
+                    write_record_int(j, mrec);
                 } else {
-                    move = false;
-                    m = static_cast<double>(st.L);
+                    mrec = st.L;
                     st.L = P.L0;
                     st.stays += 1;
                     int ns = st.set_start + k;
@@ -742,16 +761,36 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                     st.period_start = static_cast<int64_t>(step) + 1;
                     list_valid = false;
                     period_end = true;
+                    write_record_int(-1, mrec);
                 }
-            }
-            if (move) {
-                if (sat) st.saturated += 1;
-                apply_move(j, always_move);
-                st.E = __dadd_rn(st.E, A::tod(dj));
-                st.flips += 1;
-                write_record(j, m);
             } else {
-                write_record(-1, m);
+                double m = mult_md(mu);
+                if (variant == VAR_UNBIASED) {
+                    const bool fits = mu.mi >= 0 ? mu.mi <= st.L : m <= static_cast<double>(st.L);
+                    if (fits) {
+                        st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(m);
+                    } else {
+                        move = false;
+                        m = static_cast<double>(st.L);
+                        st.L = P.L0;
+                        st.stays += 1;
+                        int ns = st.set_start + k;
+                        while (ns >= n) ns -= n;
+                        st.set_start = ns;
+                        st.period_start = static_cast<int64_t>(step) + 1;
+                        list_valid = false;
+                        period_end = true;
+                    }
+                }
+                if (move) {
+                    if (sat) st.saturated += 1;
+                    apply_move(j, always_move);
+                    st.E = __dadd_rn(st.E, A::tod(dj));
+                    st.flips += 1;
+                    write_record(j, m);
+                } else {
+                    write_record(-1, m);
+                }
             }
         }
         const bool improved = st.E < st.best_E;  // (the same for every thread of the team)
@@ -863,6 +902,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
         for (int w = ctid; w < ld / 32; w += TCC) gx[w] = xw[w];
     }
     if (ctid == 0) {
+        st.sum_m = __dadd_rn(st.sum_m, static_cast<double>(sum_int));
         st.tape_records = tape_pos < P.tape_cap ? tape_pos : P.tape_cap;
         if (!P.tape) st.tape_records = 0;
         P.state[cid] = st;

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2210_10513_gb300 import synth
-from tests.gpu_helpers import assert_chain_equal, gpu_run, oracle_run
+from tests.gpu_helpers import assert_chain_equal, gpu_run, oracle_run, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -125,3 +125,33 @@ def test_sweep_not_used_with_too_many_sets(monkeypatch):
     p = _problem(1000, -10, 10, 5, np.int32, 0.1)
     g = gpu_run([p], 200, tape=True, variant="unbiased", k=64, chains_per_replica=2, seed=1, L0=100)
     assert g["info"].set_sweep == 0 and g["info"].spec_depth == 8
+
+
+@pytest.mark.parametrize("sweep", ["1", "0"])
+def test_sweep_sample_tape(monkeypatch, sweep):
+    # tape = 2: the state and energy each record starts from.  The bits are
+    # the initial state (all zeros) with the earlier records' flips applied;
+    # the energy is x^T Q x + b^T x of those bits, exact for integer Q.
+    from paper_2210_10513_gb300 import pns
+    monkeypatch.setenv("PNS_SPEC_DEPTH", "8" if sweep == "1" else "0")
+    monkeypatch.setenv("PNS_SWEEP", sweep)
+    n, recs = 256, 1500
+    p = _problem(n, -40, 40, 12, np.int32, 0.1)
+    s = pns.Sampler([dict(n=n, q=to_dev(p["q"]), b=to_dev(p["b"]), betas=p["betas"])], variant="unbiased", k=16,
+                    chains_per_replica=3, L0=100, seed=21, tape=2)
+    assert s.info.set_sweep == int(sweep)
+    s.run(recs)
+    out = s.read()
+    xb, E = s.samples()
+    s.close()
+    q = p["q"].astype(np.int64)
+    bvec = p["b"].astype(np.int64)
+    for cid in range(3):
+        x = np.zeros(n, dtype=np.int64)
+        bits = synth.unpack_bits(xb[cid, :recs], n)
+        for r in range(recs):
+            np.testing.assert_array_equal(bits[r], x, err_msg="state at record %d, chain %d" % (r, cid))
+            assert E[cid, r] == float(x @ q @ x + bvec @ x), (cid, r)
+            j = out["flips"][cid, r]
+            if j >= 0:
+                x[j] ^= 1

@@ -121,12 +121,15 @@ def test_consecutive_runs_continue_the_chain():
     np.testing.assert_array_equal(two["states"], one["states"])
 
 
-def test_checkpoint_restore_bit_identical():
+@pytest.mark.parametrize("subset", ["random", "systematic"])
+def test_checkpoint_restore_bit_identical(subset):
+    # (random sets: the speculative kernel; systematic: the set sweep)
     from paper_2210_10513_gb300 import pns
     from tests.gpu_helpers import to_dev
     p = dict(n=100, q=synth.dense_normal(100, 1.0, 8), b=synth.vector_normal(100, 1.0, 8), betas=[0.5])
     s = pns.Sampler([dict(n=100, q=to_dev(p["q"]), b=to_dev(p["b"]), betas=[0.5])], variant="unbiased", k=10,
-                    subset="random", chains_per_replica=4, seed=3, tape=True)
+                    subset=subset, chains_per_replica=4, seed=3, tape=True)
+    assert s.info.set_sweep == (1 if subset == "systematic" else 0)
     s.run(500)
     ck = s.checkpoint()
     s.run(600)

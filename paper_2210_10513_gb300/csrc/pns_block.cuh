@@ -261,25 +261,29 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
             e = record_draws(seed, chain_id, step, n, false, true).e1;
         };
         draws(static_cast<uint64_t>(st.step), ex, e1);
-        // deferred tape entry (written one record late)
+        // deferred tape entry (written one record late).  The multiplicities
+        // are integers <= L0: the period's sum is kept in int64 and added to
+        // the fp64 sum at the period end (exact: every partial sum is an
+        // integer below 2^53), and the fp64 M is formed only for the tape
         int32_t pend_flip = 0;
-        double pend_m = 0.0;
+        int64_t pend_m = 0;
         int64_t pend_pos = -1;
-        // (the fp64 sum of M and the running minimum of E are also taken one
-        // record late, when their operands are long ready)
+        int64_t sum_i = 0;
+        // (the running minimum of E is also taken one record late, when its
+        // operand is long ready)
         auto flush_record = [&]() {
             if (pend_pos >= 0) {
                 if (lane == 0 && P.tape >= 1 && pend_pos < P.tape_cap) {
                     const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + pend_pos;
                     P.tape_flip[o] = pend_flip;
-                    P.tape_m[o] = pend_m;
+                    P.tape_m[o] = static_cast<double>(pend_m);
                 }
-                st.sum_m = __dadd_rn(st.sum_m, pend_m);
+                sum_i += pend_m;
                 st.best_E = fmin(st.best_E, st.E);
             }
             pend_pos = -1;
         };
-        auto write_record = [&](int32_t flip, double m) {  // flushed at the start of the next record
+        auto write_record = [&](int32_t flip, int64_t m) {  // flushed at the start of the next record
             pend_flip = flip;
             pend_m = m;
             pend_pos = st.step - step0;
@@ -363,13 +367,14 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) ex[u] = exn[u];
             e1 = e1n;
-            double m = mult_md(mu);
             const D dj = delta_t(a, j);
             __syncwarp();
             bool period_end = false;
             const bool fits = mult_fits_small(mu, static_cast<int32_t>(st.L));  // (L0 < 2^31 here)
             if (fits) {
-                st.L -= mu.mi >= 0 ? mu.mi : static_cast<int64_t>(__float2int_rz(mu.fgl)) + 1;
+                // (a move's M fits the budget: below 2^31, exact)
+                const int64_t m = mu.mi >= 0 ? mu.mi : static_cast<int64_t>(__float2int_rz(mu.fgl)) + 1;
+                st.L -= m;
                 if (mu.sat) st.saturated += 1;
                 const bool up = ((xw[j >> 5] >> (j & 31)) & 1u) == 0u;
                 if (lane == 0) prefetch_l2(Q + static_cast<int64_t>(j) * ld, row_bytes);
@@ -393,7 +398,7 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
                     len = 0;
                 }
             } else {
-                m = static_cast<double>(st.L);
+                const int64_t m = st.L;
                 st.L = P.L0;
                 st.stays += 1;
                 int ns = st.set_start + k;
@@ -410,6 +415,7 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const KParams P) {
         while (!one_record()) {
         }
         flush_record();
+        st.sum_m = __dadd_rn(st.sum_m, static_cast<double>(sum_i));
         __syncwarp();
         if (lane == 0) {
             *cst(s) = st;

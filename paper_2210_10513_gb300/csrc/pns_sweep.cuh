@@ -1,17 +1,18 @@
 // pns_sweep.cuh -- set-sweep evaluation of Unbiased PNS with systematic sets.
 //
 // With systematic sets the chain cycles through I = n / gcd(n, k) partial
-// neighbour sets (Section 4.2's deterministic order), and a record that stays
-// ends its period without changing the state (x, h, E).  For a fixed state,
-// everything a record computes except its own random numbers is therefore a
-// function of the set alone: the deltas, the anchor, the weights, their
-// quantised sum and the move probability p (Algorithm 6 with the uniform
-// proposal, Eq. for Q_i).  This kernel evaluates all I sets of the current
-// state once -- the D warps of a chain own I / D sets each and leave p,
-// -ln(1 - p) and the weights in shared memory -- and then one warp alone
-// decides the records 32 at a time: record r lies on set (s0 + r) mod I, its
-// budget is the current L for r = 0 and L0 after a stay, and it moves iff its
-// multiplicity 1 + Geom(p) fits the budget.  Stays are committed in closed
+// neighbour sets of k consecutive bits, each starting k bits after the last
+// (Sec. 5, the wrap-around sets of size 14 for n = 16), and a record that
+// stays ends its period without changing the state (x, h, E).  For a fixed
+// state, everything a record computes except its own random numbers is
+// therefore a function of the set alone: the deltas, the anchor, the weights,
+// their quantised sum and the move probability p (Algorithm 6 with the
+// uniform proposal over the set).  This kernel evaluates all I sets of the
+// current state once -- the D warps of a chain own I / D sets each and leave
+// p, -ln(1 - p) and the weights in shared memory -- and then one warp alone
+// decides the records 32 at a time: record r lies on set (s0 + r k / g) mod I
+// (g = gcd(n, k)), its budget is the current L for r = 0 and L0 after a stay,
+// and it moves iff its multiplicity 1 + Geom(p) fits the budget.  Stays are committed in closed
 // form without a barrier; the first mover's race (Proposition 5) reads its
 // set's weights, and that warp applies the row before the team evaluates the
 // new state.  The other warps wait at the barrier meanwhile, so the issue

@@ -155,3 +155,17 @@ def test_sweep_sample_tape(monkeypatch, sweep):
             j = out["flips"][cid, r]
             if j >= 0:
                 x[j] ^= 1
+
+
+@pytest.mark.parametrize("n,k,L0", [(64, 64, 100), (32, 1, 100), (40, 5, 1), (40, 5, 7)])
+def test_sweep_edge_shapes(monkeypatch, n, k, L0):
+    # one set (k = n), 32 one-bit sets (k = 1), and budgets of 1 and 7 original
+    # samples (many records end a period on an exact budget)
+    _sweep(monkeypatch)
+    p = _problem(n, -20, 20, 31, np.int32, 0.3)
+    cfg = dict(variant="unbiased", k=k, chains_per_replica=3, seed=8, L0=L0)
+    g = gpu_run([p], 1200, tape=True, **cfg)
+    assert g["info"].set_sweep == 1
+    ref = oracle_run([p], 1200, list(range(3)), **cfg)
+    for cid in range(3):
+        assert_chain_equal(g, ref[cid], cid, n, 1200)

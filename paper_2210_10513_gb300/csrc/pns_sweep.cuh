@@ -9,10 +9,11 @@
 // their quantised sum and the move probability p (Algorithm 6 with the
 // uniform proposal over the set).  This kernel evaluates all I sets of the
 // current state once -- the D warps of a chain own I / D sets each and leave
-// p, -ln(1 - p) and the weights in shared memory -- and then one warp alone
+// p and the weights in shared memory -- and then one warp alone
 // decides the records 32 at a time: record r lies on set (s0 + r k / g) mod I
 // (g = gcd(n, k)), its budget is the current L for r = 0 and L0 after a stay,
-// and it moves iff its multiplicity 1 + Geom(p) fits the budget.  Stays are committed in closed
+// and it moves iff its multiplicity 1 + Geom(p) fits the budget (each lane
+// takes -ln(1 - p) of its record's set beside its Exp(1)).  Stays are committed in closed
 // form without a barrier; the first mover's race (Proposition 5) reads its
 // set's weights, and that warp applies the row before the team evaluates the
 // new state.  The other warps wait at the barrier meanwhile, so the issue
@@ -29,8 +30,8 @@ struct SweepSmem {
     int32_t fields, xw, table, wts, kpad, ctl, total;
 };
 
-// Per chain: fields, bits, per set (p, -ln(1 - p)), per set the k weights,
-// a control word.
+// Per chain: fields, bits, per set p (and a spare word), per set the k
+// weights, a control word.
 PNS_HD SweepSmem sweep_smem(int32_t ld, int32_t hbytes, int32_t k, int32_t nsets) {
     SweepSmem s;
     s.fields = 0;
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     };
 
     while (done < P.steps) {
-        // ---- every set of the current state: p, -ln(1 - p), weights --------
+        // ---- every set of the current state: p and the weights ---------------
         {
             // the warp's sets in lockstep (a warp without an own set evaluates
             // a copy of another and stores nothing)
@@ -199,8 +200,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                     }
                 }
             }
-            // the per-set scalars, lane u for set u: anchor e^{-beta A},
-            // p and -ln(1 - p)
+            // the per-set scalars, lane u for set u: anchor e^{-beta A} and p
             float af = 0.0f;
             int32_t ai = 0;
             uint64_t S = 0;
@@ -223,8 +223,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
             else anchor_e = det_expf(-__fmul_rn(beta, af));
             const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
             const float p = mult_p(S, k, anchor_f);
-            const float c = det_neg_log1m(p);  // (used only when 0 < p < 1)
-            if (lane < SPW && my_own) table[my_sg] = make_float2(p, c);
+            if (lane < SPW && my_own) table[my_sg] = make_float2(p, 0.0f);
         }
         sync_team();
         // ---- warp wser: records 32 at a time up to the first mover ----------
@@ -240,7 +239,9 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 // (every lane decides; lanes past the last record are masked)
                 const float2 pc = table[sg];
                 const float e1 = record_draws(seed, chain_id, step0 + lane, n, false, true).e1;
-                const Mult mu = mult_from(pc.x, pc.y, e1);
+                // -ln(1 - p) of the record's set (used only when 0 < p < 1),
+                // evaluated beside its Exp(1)
+                const Mult mu = mult_from(pc.x, det_neg_log1m(pc.x), e1);
                 const bool fits =
                     lane < nb && mult_fits_small(mu, static_cast<int32_t>(lane == 0 ? st.L : P.L0));  // (L0 < 2^31)
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fits);

@@ -9,11 +9,12 @@
 // their quantised sum and the move probability p (Algorithm 6 with the
 // uniform proposal over the set).  This kernel evaluates all I sets of the
 // current state once -- the D warps of a chain own I / D sets each and leave
-// p and the weights in shared memory -- and then one warp alone
+// the quantised weight sum S, the anchor factor and the weights in shared
+// memory -- and then one warp alone
 // decides the records 32 at a time: record r lies on set (s0 + r k / g) mod I
 // (g = gcd(n, k)), its budget is the current L for r = 0 and L0 after a stay,
 // and it moves iff its multiplicity 1 + Geom(p) fits the budget (each lane
-// takes -ln(1 - p) of its record's set beside its Exp(1)).  Stays are committed in closed
+// forms p and -ln(1 - p) of its record's set beside its Exp(1)).  Stays are committed in closed
 // form without a barrier; the first mover's race (Proposition 5) reads its
 // set's weights, and that warp applies the row before the team evaluates the
 // new state.  The other warps wait at the barrier meanwhile, so the issue
@@ -30,15 +31,15 @@ struct SweepSmem {
     int32_t fields, xw, table, wts, kpad, ctl, total;
 };
 
-// Per chain: fields, bits, per set p (and a spare word), per set the k
-// weights, a control word.
+// Per chain: fields, bits, per set S and e^{-beta A}, per set the k weights,
+// a control word.
 PNS_HD SweepSmem sweep_smem(int32_t ld, int32_t hbytes, int32_t k, int32_t nsets) {
     SweepSmem s;
     s.fields = 0;
     s.xw = round16(ld * hbytes);
     s.table = s.xw + round16(ld / 8);
     s.kpad = (k + 3) & ~3;
-    s.wts = s.table + round16(8 * nsets);
+    s.wts = s.table + 16 * nsets;
     s.ctl = s.wts + 4 * s.kpad * nsets;
     s.total = s.ctl + 16;
     return s;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     unsigned char *base = smem + chd.smem_off;
     HT *h = reinterpret_cast<HT *>(base + L.fields);
     uint32_t *xw = reinterpret_cast<uint32_t *>(base + L.xw);
-    float2 *table = reinterpret_cast<float2 *>(base + L.table);
+    uint4 *table = reinterpret_cast<uint4 *>(base + L.table);  // per set: S (lo, hi), e^{-beta A} bits
     float *wts = reinterpret_cast<float *>(base + L.wts);
     volatile int32_t *ctl = reinterpret_cast<volatile int32_t *>(base + L.ctl);
     const CT *bvec = reinterpret_cast<const CT *>(in.b);
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     };
 
     while (done < P.steps) {
-        // ---- every set of the current state: p and the weights ---------------
+        // ---- every set of the current state: S, e^{-beta A}, the weights -----
         {
             // the warp's sets in lockstep (a warp without an own set evaluates
             // a copy of another and stores nothing)
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                     }
                 }
             }
-            // the per-set scalars, lane u for set u: anchor e^{-beta A} and p
+            // the per-set scalars, lane u for set u: S and the anchor e^{-beta A}
             float af = 0.0f;
             int32_t ai = 0;
             uint64_t S = 0;
@@ -222,8 +223,9 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
             if (tabled) anchor_e = __ldg(wtab + (ai < wt_n ? ai : wt_n - 1)).x;
             else anchor_e = det_expf(-__fmul_rn(beta, af));
             const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
-            const float p = mult_p(S, k, anchor_f);
-            if (lane < SPW && my_own) table[my_sg] = make_float2(p, 0.0f);
+            if (lane < SPW && my_own)
+                table[my_sg] = make_uint4(static_cast<uint32_t>(S), static_cast<uint32_t>(S >> 32),
+                                          __float_as_uint(anchor_f), 0u);
         }
         sync_team();
         // ---- warp wser: records 32 at a time up to the first mover ----------
@@ -237,11 +239,12 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 int sg = sig0 + (lane * kstep) % nsets;  // set of record lane after lane stays
                 sg = sg >= nsets ? sg - nsets : sg;
                 // (every lane decides; lanes past the last record are masked)
-                const float2 pc = table[sg];
+                const uint4 te = table[sg];
                 const float e1 = record_draws(seed, chain_id, step0 + lane, n, false, true).e1;
-                // -ln(1 - p) of the record's set (used only when 0 < p < 1),
-                // evaluated beside its Exp(1)
-                const Mult mu = mult_from(pc.x, det_neg_log1m(pc.x), e1);
+                // p and -ln(1 - p) (used only when 0 < p < 1) of the record's
+                // set, evaluated beside its Exp(1)
+                const float p = mult_p((static_cast<uint64_t>(te.y) << 32) | te.x, k, __uint_as_float(te.z));
+                const Mult mu = mult_from(p, det_neg_log1m(p), e1);
                 const bool fits =
                     lane < nb && mult_fits_small(mu, static_cast<int32_t>(lane == 0 ? st.L : P.L0));  // (L0 < 2^31)
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fits);

@@ -9,12 +9,12 @@
 // their quantised sum and the move probability p (Algorithm 6 with the
 // uniform proposal over the set).  This kernel evaluates all I sets of the
 // current state once -- the D warps of a chain own I / D sets each and leave
-// the quantised weight sum S, the anchor factor and the weights in shared
-// memory -- and then one warp alone
+// the quantised weight sum S, the anchor A and the weights in shared memory
+// -- and then one warp alone
 // decides the records 32 at a time: record r lies on set (s0 + r k / g) mod I
 // (g = gcd(n, k)), its budget is the current L for r = 0 and L0 after a stay,
 // and it moves iff its multiplicity 1 + Geom(p) fits the budget (each lane
-// forms p and -ln(1 - p) of its record's set beside its Exp(1)).  Stays are committed in closed
+// forms e^{-beta A}, p and -ln(1 - p) of its record's set beside its Exp(1)).  Stays are committed in closed
 // form without a barrier; the first mover's race (Proposition 5) reads its
 // set's weights, and that warp applies the row before the team evaluates the
 // new state.  The other warps wait at the barrier meanwhile, so the issue
@@ -31,8 +31,8 @@ struct SweepSmem {
     int32_t fields, xw, table, wts, kpad, ctl, total;
 };
 
-// Per chain: fields, bits, per set S and e^{-beta A}, per set the k weights,
-// a control word.
+// Per chain: fields, bits, per set S and A, per set the k weights, a control
+// word.
 PNS_HD SweepSmem sweep_smem(int32_t ld, int32_t hbytes, int32_t k, int32_t nsets) {
     SweepSmem s;
     s.fields = 0;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     unsigned char *base = smem + chd.smem_off;
     HT *h = reinterpret_cast<HT *>(base + L.fields);
     uint32_t *xw = reinterpret_cast<uint32_t *>(base + L.xw);
-    uint4 *table = reinterpret_cast<uint4 *>(base + L.table);  // per set: S (lo, hi), e^{-beta A} bits
+    uint4 *table = reinterpret_cast<uint4 *>(base + L.table);  // per set: S (lo, hi), A's key bits
     float *wts = reinterpret_cast<float *>(base + L.wts);
     volatile int32_t *ctl = reinterpret_cast<volatile int32_t *>(base + L.ctl);
     const CT *bvec = reinterpret_cast<const CT *>(in.b);
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
     };
 
     while (done < P.steps) {
-        // ---- every set of the current state: S, e^{-beta A}, the weights -----
+        // ---- every set of the current state: S, A, the weights ---------------
         {
             // the warp's sets in lockstep (a warp without an own set evaluates
             // a copy of another and stores nothing)
@@ -201,9 +201,8 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                     }
                 }
             }
-            // the per-set scalars, lane u for set u: S and the anchor e^{-beta A}
-            float af = 0.0f;
-            int32_t ai = 0;
+            // the per-set scalars, lane u for set u: S and the anchor A
+            uint32_t abits = 0u;
             uint64_t S = 0;
             int my_sg = 0;
             bool my_own = false;
@@ -212,20 +211,14 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 const uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa[u]);
                 const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb[u]);
                 if (lane == u) {
-                    af = A::tof(amin[u]);
-                    if constexpr (!std::is_same<HT, float>::value) ai = amin[u];
+                    abits = A::key(amin[u]);
                     S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
                     my_sg = sg[u];
                     my_own = own[u];
                 }
             }
-            float anchor_e;
-            if (tabled) anchor_e = __ldg(wtab + (ai < wt_n ? ai : wt_n - 1)).x;
-            else anchor_e = det_expf(-__fmul_rn(beta, af));
-            const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
             if (lane < SPW && my_own)
-                table[my_sg] = make_uint4(static_cast<uint32_t>(S), static_cast<uint32_t>(S >> 32),
-                                          __float_as_uint(anchor_f), 0u);
+                table[my_sg] = make_uint4(static_cast<uint32_t>(S), static_cast<uint32_t>(S >> 32), abits, 0u);
         }
         sync_team();
         // ---- warp wser: records 32 at a time up to the first mover ----------
@@ -241,9 +234,19 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_sweep_kernel(c
                 // (every lane decides; lanes past the last record are masked)
                 const uint4 te = table[sg];
                 const float e1 = record_draws(seed, chain_id, step0 + lane, n, false, true).e1;
-                // p and -ln(1 - p) (used only when 0 < p < 1) of the record's
-                // set, evaluated beside its Exp(1)
-                const float p = mult_p((static_cast<uint64_t>(te.y) << 32) | te.x, k, __uint_as_float(te.z));
+                // e^{-beta A}, p and -ln(1 - p) (used only when 0 < p < 1) of
+                // the record's set, evaluated beside its Exp(1)
+                const D_t amin = A::unkey(te.z);
+                const float af = A::tof(amin);
+                float anchor_e;
+                if constexpr (!std::is_same<HT, float>::value) {
+                    if (wt_n > 0) anchor_e = __ldg(wtab + (amin < wt_n ? amin : wt_n - 1)).x;  // (uniform)
+                    else anchor_e = det_expf(-__fmul_rn(beta, af));
+                } else {
+                    anchor_e = det_expf(-__fmul_rn(beta, af));
+                }
+                const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
+                const float p = mult_p((static_cast<uint64_t>(te.y) << 32) | te.x, k, anchor_f);
                 const Mult mu = mult_from(p, det_neg_log1m(p), e1);
                 const bool fits =
                     lane < nb && mult_fits_small(mu, static_cast<int32_t>(lane == 0 ? st.L : P.L0));  // (L0 < 2^31)

@@ -169,3 +169,18 @@ def test_sweep_edge_shapes(monkeypatch, n, k, L0):
     ref = oracle_run([p], 1200, list(range(3)), **cfg)
     for cid in range(3):
         assert_chain_equal(g, ref[cid], cid, n, 1200)
+
+
+def test_sweep_weight_table_per_temperature(monkeypatch):
+    # one integer instance at four temperatures without exchange: every chain
+    # takes the weight table of its own beta (beta = 0.005 has none and uses
+    # the exponential itself)
+    _sweep(monkeypatch)
+    p = _problem(256, -60, 60, 41, np.int32, 0.05)
+    p["betas"] = [0.05, 0.1, 0.5, 0.005]
+    cfg = dict(variant="unbiased", k=16, chains_per_replica=2, seed=6, L0=100)
+    g = gpu_run([p], 1500, tape=True, **cfg)
+    assert g["info"].set_sweep == 1
+    ref = oracle_run([p], 1500, list(range(8)), **cfg)
+    for cid in range(8):
+        assert_chain_equal(g, ref[cid], cid, 256, 1500)

@@ -98,3 +98,31 @@ def test_blocked_matches_oracle(monkeypatch):
             assert g["stats"][cid]["energy"] == res[s]["state"].E
             bits = synth.unpack_bits(g["states"][cid:cid + 1], pr["n"])[0]
             np.testing.assert_array_equal(bits, res[s]["x"])
+
+
+@pytest.mark.parametrize("L0,swap", [(100, 100), (1000, 2000)])
+def test_blocked_sample_tape_equals_per_flip(monkeypatch, L0, swap):
+    """tape = 2: the bits and energy each record starts from.  The blocked
+    kernel sums a period's energies when it settles the period's log (and in
+    the middle of a period whose log fills up); the per-flip kernel record by
+    record: the same values."""
+    from paper_2210_10513_gb300 import pns
+    from tests.gpu_helpers import to_dev
+    betas = synth.geometric_ladder(0.01, 1.0, 4)
+    probs = _probs([200, 333], "f32", betas, seed=9)
+    out = {}
+    for blocked in ("1", "0"):
+        monkeypatch.setenv("PNS_BLOCKED", blocked)
+        s = pns.Sampler([dict(p, q=to_dev(p["q"])) for p in probs], variant="unbiased", k=1, L0=L0,
+                        swap_interval=swap, seed=12, tape=2)
+        assert s.info.period_blocked == int(blocked)
+        s.run(4000)
+        r = s.read()
+        x, e = s.samples()
+        s.close()
+        out[blocked] = (r, x, e)
+    (ra, xa, ea), (rb, xb, eb) = out["1"], out["0"]
+    np.testing.assert_array_equal(ra["stats"], rb["stats"])
+    for cid, rec in enumerate(ra["stats"]["tape_records"]):
+        np.testing.assert_array_equal(xa[cid, :rec], xb[cid, :rec])
+        np.testing.assert_array_equal(ea[cid, :rec], eb[cid, :rec])

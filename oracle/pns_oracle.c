@@ -24,7 +24,7 @@
  * kernels decide in; fields and energies of integer QUBOs are exact integers.
  * Compile with contraction off:  gcc -O2 -ffp-contract=off -fno-fast-math.
  *
- * Conventions (the paper is silent on them; readings listed in the design doc):
+ * Conventions (readings taken where the paper is silent):
  *  - local fields h = Qx + b (Q symmetric); flip delta of bit i:
  *      Delta_i = s_i * (2 h_i - b_i) + Q_ii,  s_i = 1 - 2 x_i
  *    which is E(x xor e_i) - E(x) for E = x^T Q x + b^T x.

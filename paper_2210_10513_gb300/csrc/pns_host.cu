@@ -191,6 +191,29 @@ struct PlanOut {
     bool resident = true;  // every CTA fits on the GPU at once (blocked kernel: checked)
 };
 
+// Placement of exchange-group CTAs when the grid has more CTAs than SMs but
+// fewer than two per SM.  The block scheduler gives CTAs 0 .. S-1 one SM each
+// (S SMs) and CTAs S .. C-1 to SMs 0 .. C-S-1 again, so the CTAs at positions
+// C-S .. S-1 run alone on their SM.  The pack places groups largest first and
+// pairs the largest instances with the smallest in its first CTAs: those hold
+// the slowest groups (the longest rows and widest sets, or the most records
+// per period for the hottest replica), and they move to the positions that
+// run alone.  Placement changes no result: a group's draws and arithmetic do
+// not depend on its CTA.  PNS_PLACE_ALONE=0 keeps the packed order.
+static void place_heavy_alone(PlanOut &o, int num_sms) {
+    const int C = static_cast<int>(o.cta.size());
+    if (C <= num_sms || C >= 2 * num_sms) return;
+    if (const char *e = getenv("PNS_PLACE_ALONE"))
+        if (!atoi(e)) return;
+    const int alone = 2 * num_sms - C;  // SMs that hold one CTA
+    std::vector<CtaDesc> v;
+    v.reserve(C);
+    v.insert(v.end(), o.cta.begin() + alone, o.cta.begin() + num_sms);
+    v.insert(v.end(), o.cta.begin(), o.cta.begin() + alone);
+    v.insert(v.end(), o.cta.begin() + num_sms, o.cta.end());
+    o.cta.swap(v);
+}
+
 // Packs chains (or whole exchange groups) into CTAs.  Units are placed in
 // decreasing order of shared-memory need; a CTA takes units until it reaches
 // the team limit, the shared-memory limit or its share of the work.
@@ -307,6 +330,7 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
                 break;
             }
         }
+        if (out.resident) place_heavy_alone(out, num_sms);
         return PNS_OK;
     }
     int64_t target = (static_cast<int64_t>(units.size()) + num_sms - 1) / num_sms;

@@ -76,6 +76,32 @@ def test_blocked_set_shapes(monkeypatch, n, k):
           chains_per_replica=2)
 
 
+def test_blocked_placement_changes_nothing(monkeypatch):
+    """200 exchange groups, one CTA each: more CTAs than SMs, fewer than two
+    per SM, so the planner moves the first CTAs of its pack (the largest and
+    smallest instances) to the SMs that hold one CTA.  The records do not
+    depend on where a group runs."""
+    monkeypatch.setenv("PNS_BLOCKED", "1")
+    monkeypatch.setenv("PNS_GROUP_WARPS", "4")
+    betas = synth.geometric_ladder(0.1, 5.0, 4)
+    rng = np.random.default_rng(11)
+    probs = _probs([int(v) for v in rng.integers(32, 160, 200)], "i32", betas, seed=100, kdiv=8)
+    cfg = dict(variant="unbiased", k=1, L0=50, swap_interval=100, seed=5)
+    out = {}
+    for place in ("1", "0"):
+        monkeypatch.setenv("PNS_PLACE_ALONE", place)
+        out[place] = gpu_run(probs, 600, tape=True, **cfg)
+        assert out[place]["info"].period_blocked == 1
+    a, b = out["1"], out["0"]
+    assert a["info"].ctas == b["info"].ctas
+    np.testing.assert_array_equal(a["stats"], b["stats"])
+    np.testing.assert_array_equal(a["states"], b["states"])
+    np.testing.assert_array_equal(a["fields"], b["fields"])
+    np.testing.assert_array_equal(a["flips"], b["flips"])
+    np.testing.assert_array_equal(a["m"], b["m"])
+    assert a["stats"]["swaps_accepted"].sum() > 0
+
+
 def test_blocked_matches_oracle(monkeypatch):
     monkeypatch.setenv("PNS_BLOCKED", "1")
     ns = [130, 97]

@@ -240,6 +240,8 @@ pns_status pns_energy_grads(int32_t n, float beta, const pns_moment_scalars *sca
  * field_bytes each, integers or fp32 per pns_info) to `out`. */
 pns_status pns_fields(pns_ctx *ctx, void *out, void *stream);
 
+/* Fills `info` (host memory) with the context's sizes and the launch mapping
+ * in use (kernel form, CTAs, warps per chain); no device work. */
 pns_status pns_get_info(const pns_ctx *ctx, pns_info *info);
 
 /* Serialises every chain's state (statistics, bits, fields, exchange counters)
@@ -249,7 +251,11 @@ pns_status pns_get_info(const pns_ctx *ctx, pns_info *info);
 pns_status pns_checkpoint(pns_ctx *ctx, void *buf, size_t *bytes);
 pns_status pns_restore(pns_ctx *ctx, const void *buf, size_t bytes);
 
+/* Frees the context's device memory and captured graph (cudaFree waits for
+ * the device's outstanding work); NULL is ignored. */
 void pns_destroy(pns_ctx *ctx);
+/* The message of the last failed call on this thread (thread-local storage
+ * owned by the library; valid until the thread's next failing call). */
 const char *pns_last_error(void);
 
 /* ---- Continuous state space: Unbiased PNS for continuous targets -------------

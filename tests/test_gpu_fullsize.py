@@ -227,3 +227,59 @@ def test_fit_n64_8192_chains_full_size():
         assert st["energy"][cid] == ref[cid]["state"].E
         np.testing.assert_array_equal(g["fields"][cid, :n].view(np.uint32),
                                       ref[cid]["h"].astype(np.float32).view(np.uint32))
+
+
+def test_headline_basic_full_size():
+    """The headline instance with Basic PNS (a fresh random 64-subset every
+    record, every record a move), 256 chains, one launch of 10,000 records."""
+    wl = synth.workload_dense_int1024(0)
+    n, k, recs = 1024, 64, 10000
+    p = dict(n=n, q=wl["q"], b=wl["b"], betas=[wl["beta"]])
+    cfg = dict(variant="basic", k=k, chains_per_replica=256, seed=0, graph=True)
+    g = gpu_run([p], recs, tape=True, **cfg)
+    st = g["stats"]
+    flips, ms = _concat(g, "flips"), _concat(g, "m")
+    q64 = wl["q"].astype(np.float64)
+    b64 = wl["b"].astype(np.float64)
+    bits = synth.unpack_bits(g["states"], n).astype(np.float64)
+    for cid in range(256):
+        assert len(flips[cid]) == recs and (flips[cid] >= 0).all() and (flips[cid] < n).all()
+        # (M reaches 1e20 here: the chain's fp64 sum is taken in record order)
+        assert (ms[cid] >= 1).all() and st["sum_m"][cid] == np.cumsum(ms[cid])[-1]
+        np.testing.assert_array_equal(bits[cid], _replayed_bits(flips[cid], n), err_msg="chain %d" % cid)
+    assert (st["flips"] == recs).all()
+    E = np.einsum("ci,ci->c", bits @ q64, bits) + bits @ b64
+    np.testing.assert_array_equal(st["energy"], E)
+    np.testing.assert_array_equal(g["fields"][:, :n].astype(np.float64), bits @ q64 + b64)
+    ids = [0, 129, 255]
+    ref = oracle_run([p], recs, ids, **cfg)
+    for cid in ids:
+        np.testing.assert_array_equal(flips[cid], ref[cid]["flips"], err_msg="flip tape, chain %d" % cid)
+        np.testing.assert_array_equal(ms[cid], ref[cid]["m"], err_msg="multiplicities, chain %d" % cid)
+        assert st["energy"][cid] == ref[cid]["state"].E
+
+
+def test_donuts_65536_chains_full_size():
+    """Continuous Unbiased PNS (Algorithm 7) on the Donuts target: 65,536
+    chains from the circle of radius 3, 50 neighbours, L0 = 1000, 4000 records
+    per chain.  Every chain: sum M = L0 * stays + (L0 - L); sampled chains
+    (with the one that moved most) equal the oracle bit for bit."""
+    from paper_2210_10513_gb300 import pns
+    chains, steps, L0 = 65536, 4000, 1000
+    mu0, sigma = 9.0, 0.1
+    c = 1.0 / (2 * sigma * sigma)
+    rng = np.random.default_rng(0)
+    ang = rng.uniform(0, 2 * np.pi, chains)
+    x0 = np.stack([3 * np.cos(ang), 3 * np.sin(ang)], 1).astype(np.float32)
+    st = pns.pns_donuts_run("unbiased", chains, steps, x0=x0, mu0=mu0, c=c, L0=L0, seed=100)
+    assert (st["records"] == steps).all()
+    stays = st["records"] - st["moves"]
+    np.testing.assert_array_equal(st["weight"], L0 * stays + (L0 - st["budget_left"]).astype(np.float64))
+    assert np.isfinite(st["sum_x4"]).all() and (st["sum_x2"] >= 0).all()
+    busiest = int(np.argmax(st["moves"]))
+    for ch in sorted({0, 12345, chains - 1, busiest}):
+        r = O.donuts_chain("unbiased", ch, steps, tuple(x0[ch]), mu0=mu0, c=c, L0=L0, seed=100, npairs=25)
+        for key in ("sum_x", "sum_x2", "sum_x4", "sum_pos", "x"):
+            np.testing.assert_array_equal(st[ch][key], r[key], err_msg="%s chain %d" % (key, ch))
+        for key in ("weight", "records", "moves", "budget_left", "period_start"):
+            assert st[ch][key] == r[key], (key, ch)

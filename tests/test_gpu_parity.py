@@ -208,3 +208,54 @@ def test_sharded_contexts_equal_one_context():
     b = gpu_run(probs[1:], 600, tape=True, chain_base=6, group_base=3, **cfg)
     np.testing.assert_array_equal(np.concatenate([a["flips"], b["flips"]]), whole["flips"])
     np.testing.assert_array_equal(np.concatenate([a["m"], b["m"]]), whole["m"])
+
+
+@pytest.mark.parametrize("form", ["per_flip_basic", "sweep", "spec_random", "blocked"])
+def test_zero_steps_change_nothing(form):
+    """A run of 0 records (0 original samples with exchange) changes nothing:
+    states, fields and statistics stay as created, and the next run's records
+    are those of a context that never made the empty run."""
+    from paper_2210_10513_gb300 import pns
+    from tests.gpu_helpers import to_dev
+    if form == "blocked":
+        betas = synth.geometric_ladder(0.1, 5.0, 4)
+        probs = [dict(n=96, q=synth.dense_normal(96, 1.0, 1), b=None, betas=betas, k=6)]
+        cfg = dict(variant="unbiased", k=1, L0=50, swap_interval=100, seed=3, chains_per_replica=1)
+        steps = 400
+    else:
+        probs = [_int_problem(256, lo=-40, hi=40, seed=2, dtype=np.int32, betas=(0.1,))]
+        cfg = dict(variant="basic" if form == "per_flip_basic" else "unbiased", k=16,
+                   subset="random" if form == "spec_random" else "systematic", L0=100, seed=3,
+                   chains_per_replica=4)
+        steps = 500
+
+    def make():
+        return pns.Sampler([dict(d, q=to_dev(d["q"]), b=to_dev(d.get("b"))) for d in probs], tape=True, **cfg)
+
+    a, b = make(), make()
+    info = a.info
+    want = dict(per_flip_basic=(0, 0, 0), sweep=(8, 1, 0), spec_random=(8, 0, 0), blocked=(0, 0, 1))[form]
+    assert (info.spec_depth, info.set_sweep, info.period_blocked) == want
+    before, f0 = a.read(), a.fields()
+    a.run(0)
+    after, f1 = a.read(), a.fields()
+    np.testing.assert_array_equal(before["states"], after["states"])
+    np.testing.assert_array_equal(before["stats"], after["stats"])
+    np.testing.assert_array_equal(f0, f1)
+    a.run(steps)
+    b.run(steps)
+    ra, rb = a.read(), b.read()
+    for key in ("states", "stats", "flips", "m"):
+        np.testing.assert_array_equal(ra[key], rb[key], err_msg=key)
+    np.testing.assert_array_equal(a.fields(), b.fields())
+    a.close()
+    b.close()
+
+
+def test_donuts_zero_steps():
+    from paper_2210_10513_gb300 import pns
+    x0 = np.array([[3.0, 0.5], [-1.0, 2.0], [0.0, -3.0]], np.float32)
+    st = pns.pns_donuts_run("unbiased", 3, 0, x0=x0, L0=1000, seed=1)
+    assert (st["records"] == 0).all() and (st["moves"] == 0).all() and (st["weight"] == 0).all()
+    assert (st["budget_left"] == 1000).all() and (st["period_start"] == 0).all()
+    np.testing.assert_array_equal(st["x"], x0)

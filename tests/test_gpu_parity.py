@@ -259,3 +259,23 @@ def test_donuts_zero_steps():
     assert (st["records"] == 0).all() and (st["moves"] == 0).all() and (st["weight"] == 0).all()
     assert (st["budget_left"] == 1000).all() and (st["period_start"] == 0).all()
     np.testing.assert_array_equal(st["x"], x0)
+
+
+@pytest.mark.parametrize("variant,k", [("basic", 16), ("rf", 64), ("unbiased", 16)])
+def test_saturated_multiplicity(variant, k):
+    """Q = 1000 I at beta = 1: from the all-zero state every flip costs 1000,
+    the weights underflow, p = 0 and M saturates at 2^63 (counted) for Basic
+    and RF, which move anyway; a flip back has weight 1.  Unbiased PNS cannot
+    fit a saturated M in its budget, so those records stay with M = L."""
+    n = 64
+    q = np.zeros((n, n), np.int32)
+    np.fill_diagonal(q, 1000)
+    p = dict(n=n, q=q, b=None, betas=[1.0])
+    g = _check_all([p], 400, 4, variant=variant, k=k, chains_per_replica=4, seed=9, L0=100)
+    m = g["m"][:4, :400]
+    if variant == "unbiased":
+        assert (g["stats"]["saturated"][:4] == 0).all()
+        assert (g["stats"]["stays"][:4] == 400).all() and (m == 100.0).all()
+    else:
+        assert (g["stats"]["saturated"][:4] > 0).all()
+        np.testing.assert_array_equal((m == 2.0 ** 63).sum(axis=1), g["stats"]["saturated"][:4])

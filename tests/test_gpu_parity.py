@@ -279,3 +279,13 @@ def test_saturated_multiplicity(variant, k):
     else:
         assert (g["stats"]["saturated"][:4] > 0).all()
         np.testing.assert_array_equal((m == 2.0 ** 63).sum(axis=1), g["stats"]["saturated"][:4])
+
+
+@pytest.mark.parametrize("subset", ["systematic", "random"])
+def test_largest_budget_of_the_fast_kernels(subset):
+    """L0 = 2^31 - 1, the largest budget the set-sweep and speculative kernels
+    take (their budget test runs in 32-bit integers)."""
+    p = _int_problem(128, lo=-30, hi=30, seed=6, dtype=np.int32, betas=(0.2,))
+    g = _check_all([p], 2000, 4, variant="unbiased", k=16, subset=subset, chains_per_replica=4, seed=12,
+                   L0=2 ** 31 - 1)
+    assert g["info"].spec_depth == 8 and g["info"].set_sweep == (1 if subset == "systematic" else 0)

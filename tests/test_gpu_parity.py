@@ -289,3 +289,36 @@ def test_largest_budget_of_the_fast_kernels(subset):
     g = _check_all([p], 2000, 4, variant="unbiased", k=16, subset=subset, chains_per_replica=4, seed=12,
                    L0=2 ** 31 - 1)
     assert g["info"].spec_depth == 8 and g["info"].set_sweep == (1 if subset == "systematic" else 0)
+
+
+@pytest.mark.parametrize("src,dst", [("sweep", "per_flip"), ("per_flip", "sweep"), ("per_flip", "spec")])
+def test_checkpoint_moves_between_kernel_forms(monkeypatch, src, dst):
+    """A checkpoint holds the chains, not the kernel: restored into a context
+    that runs another kernel form, the chains continue with the same records."""
+    from paper_2210_10513_gb300 import pns
+    from tests.gpu_helpers import to_dev
+    env = dict(sweep=("8", "1"), spec=("8", "0"), per_flip=("0", "0"))
+    p = _int_problem(256, lo=-40, hi=40, seed=4, dtype=np.int32, betas=(0.1,))
+
+    def make(form):
+        monkeypatch.setenv("PNS_SPEC_DEPTH", env[form][0])
+        monkeypatch.setenv("PNS_SWEEP", env[form][1])
+        s = pns.Sampler([dict(n=256, q=to_dev(p["q"]), b=to_dev(p["b"]), betas=p["betas"])], variant="unbiased",
+                        k=16, chains_per_replica=3, seed=7, L0=100, tape=True)
+        assert (s.info.spec_depth, s.info.set_sweep) == (int(env[form][0]), int(env[form][1]))
+        return s
+
+    a = make(src)
+    a.run(700)
+    ck = a.checkpoint()
+    a.run(700)
+    ra, fa = a.read(), a.fields()
+    b = make(dst)
+    b.restore(ck)
+    b.run(700)
+    rb, fb = b.read(), b.fields()
+    a.close()
+    b.close()
+    for key in ("states", "stats", "flips", "m"):
+        np.testing.assert_array_equal(ra[key], rb[key], err_msg=key)
+    np.testing.assert_array_equal(fa, fb)

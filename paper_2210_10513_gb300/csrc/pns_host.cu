@@ -664,21 +664,27 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
     pns_status st_b = run_impl(c, burn, s, false);
     if (st_b != PNS_OK) return st_b;
     CU(save(burned));
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
+    struct Events {  // (destroyed on every return path)
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Events() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } ev;
+    CU(cudaEventCreate(&ev.e0));
+    CU(cudaEventCreate(&ev.e1));
     float best_ms = 1e30f;
     Mapping best = base;
     for (const Mapping &m : cands) {
         if (apply_mapping(c, m, s) != PNS_OK) continue;
         if (run_impl(c, warm, s, false) != PNS_OK) continue;  // first launch of this kernel
         CU(load(burned));
-        CU(cudaEventRecord(e0, s));
+        CU(cudaEventRecord(ev.e0, s));
         pns_status rs = run_impl(c, probe, s, false);
-        CU(cudaEventRecord(e1, s));
-        CU(cudaEventSynchronize(e1));
+        CU(cudaEventRecord(ev.e1, s));
+        CU(cudaEventSynchronize(ev.e1));
         float ms = 0.0f;
-        CU(cudaEventElapsedTime(&ms, e0, e1));
+        CU(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
         if (rs == PNS_OK && ms < best_ms) {
             best_ms = ms;
             best = m;
@@ -686,8 +692,6 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         CU(load(burned));
     }
     CU(load(orig));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     CU(cudaStreamSynchronize(s));
     int32_t code = 0;
     CU(cudaMemcpy(&code, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));

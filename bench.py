@@ -88,7 +88,10 @@ def oracle_rate(records, chains_sample, seed=0, variant="unbiased"):
     tot = sum(r[0] for r in res)
     flips = sum(r[1] for r in res)
     summ = sum(r[2] for r in res)
+    # one core's rate: each worker runs its chains serially on one core
+    single = float(np.mean([r[0] / r[3] for r in res]))
     return dict(rate=tot / wall, flips_rate=flips / wall, orig_rate=summ / wall, wall=wall, cores=workers,
+                single_core_rate=single,
                 sample="%d chains x %d records of the same workload (chains 0..%d)" % (chains_sample, records,
                                                                                       chains_sample - 1))
 
@@ -119,7 +122,7 @@ def reference_arm(args):
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": config_desc(args.records, "flushed between timed steps (256 MiB write)"),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+                             "sample": last["sample"], "single_core_value": last["single_core_rate"]},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -328,7 +331,8 @@ def gpu_arm(args):
         build_oracle.build()
         cores = os.cpu_count() or 1
         r = oracle_rate(100000, min(CHAINS, cores))
-        cpu = {"value": r["rate"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+        cpu = {"value": r["rate"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
+               "single_core_value": r["single_core_rate"]}
     line = {
         "metric": "PNS jump samples/s (records/s)",
         "value": value * 1.0, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

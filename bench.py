@@ -230,7 +230,7 @@ def gpu_arm(args):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         after = sampler.read(tape=False)["stats"]
-        d = {k: float(after[k].sum() - before[k].sum()) for k in ("steps", "flips", "sum_m")}
+        d = {k: float(after[k].sum() - before[k].sum()) for k in ("steps", "flips", "sum_m", "saturated")}
         return ms, d
 
     s_unb = make("unbiased")
@@ -252,9 +252,9 @@ def gpu_arm(args):
         t = torch.tensor([kernel_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         kernel_s = float(t.item())
-        tot = torch.tensor([d["steps"], d["flips"], d["sum_m"]], dtype=torch.float64, device=dev)
+        tot = torch.tensor([d["steps"], d["flips"], d["sum_m"], d["saturated"]], dtype=torch.float64, device=dev)
         dist.all_reduce(tot)
-        d = dict(steps=float(tot[0]), flips=float(tot[1]), sum_m=float(tot[2]))
+        d = dict(steps=float(tot[0]), flips=float(tot[1]), sum_m=float(tot[2]), saturated=float(tot[3]))
     value = d["steps"] / kernel_s
     extra = {}
     if rank == 0 and not args.quick:
@@ -340,6 +340,7 @@ def gpu_arm(args):
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": config_desc(records, "flushed between timed steps (256 MiB write)"),
         "flips_per_s": d["flips"] / kernel_s, "original_samples_per_s": d["sum_m"] / kernel_s,
+        "saturated_moves": int(d["saturated"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "peak_kind": peak_note,
                      "algorithmic_bytes": "2048 B (one int16 row of Q) per flip"},

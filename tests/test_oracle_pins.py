@@ -362,3 +362,36 @@ def test_best_state_is_first_minimum_of_the_replayed_path(variant, k):
     first_min = int(np.argmin(e_path))  # argmin returns the first occurrence
     assert st.st.best_E == e_path[first_min]
     assert X.code_of(st.x_best) == int(path[first_min])
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.2 (Basic PNS: a fresh partial neighbour set every step) and Sec. 5
+# (random sets for Unbiased PNS: one set per period): every move flips a bit
+# of the set its record was drawn from.
+# ---------------------------------------------------------------------------
+def test_moves_lie_in_their_random_sets():
+    n, k, seed = 40, 6, 17
+    Q = synth.dense_int(n, -20, 20, seed=4, dtype=np.int32)
+    p = O.Problem(q=Q, b=None)
+    # Basic: record r draws its set at step r
+    res = O.run_independent([p], [[0.3]], dict(variant="basic", k=k, seed=seed), 2, None, 3000)
+    for cid, r in res.items():
+        f = r["flips"]
+        assert (f >= 0).all()
+        for step in range(len(f)):
+            assert f[step] in O.random_subset(n, k, seed, cid, step), (cid, step)
+    # Unbiased, random sets: the set is drawn at the period's first record and
+    # kept until a stay ends the period
+    res = O.run_independent([p], [[0.3]], dict(variant="unbiased", k=k, subset="random", L0=50, seed=seed), 2,
+                            None, 3000)
+    for cid, r in res.items():
+        f = r["flips"]
+        start = 0
+        cur = O.random_subset(n, k, seed, cid, 0)
+        for step in range(len(f)):
+            if f[step] >= 0:
+                assert f[step] in cur, (cid, step)
+            else:
+                start = step + 1
+                cur = O.random_subset(n, k, seed, cid, start)
+        assert r["state"].period_start == start

@@ -395,3 +395,24 @@ def test_moves_lie_in_their_random_sets():
                 start = step + 1
                 cur = O.random_subset(n, k, seed, cid, start)
         assert r["state"].period_start == start
+
+
+def test_moves_follow_the_wrapping_systematic_sets():
+    # Sec. 5's example, n = 16 and |N_i| = 14: a chain's i-th period uses set
+    # i mod 8 of the wrap-around sequence, and every move flips a bit of it
+    n, k = 16, 14
+    sets = X.systematic_sets(n, k)
+    Q = synth.dense_int(n, -8, 8, seed=0, dtype=np.int32)
+    p = O.Problem(q=Q, b=None)
+    res = O.run_independent([p], [[1.0]], dict(variant="unbiased", k=k, subset="systematic", L0=20, seed=3), 3,
+                            None, 4000)
+    for cid, r in res.items():
+        f = r["flips"]
+        period = 0
+        for step in range(len(f)):
+            if f[step] >= 0:
+                assert f[step] in sets[period % len(sets)], (cid, step)
+            else:
+                period += 1
+        assert r["state"].set_start == sets[period % len(sets)][0]
+        assert period == r["state"].stays

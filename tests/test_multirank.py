@@ -87,3 +87,22 @@ def test_two_rank_gloo_job_equals_single_process(tmp_path):
     assert got[0] == full["flips"] and got[1] == full["sum_m"] and got[3] == full["chains"]
     assert abs(got[2] - full["energy"]) < 1e-9 * max(1.0, abs(full["energy"]))
     assert got[4] == 2.0  # max over ranks
+
+
+def test_shard_costs_balanced():
+    """Each rank's share of the summed cost is within one instance's cost of
+    the even share, and every instance belongs to exactly one rank."""
+    rng = np.random.default_rng(3)
+    for trial in range(200):
+        n = int(rng.integers(1, 60))
+        costs = (rng.integers(128, 2049, size=n) ** 2).tolist()
+        world = int(rng.integers(1, 9))
+        spans = [shard.shard_instances(costs, world, r) for r in range(world)]
+        owned = np.zeros(n, int)
+        for a, b in spans:
+            owned[a:b] += 1
+        assert (owned == 1).all()
+        total, cmax = float(sum(costs)), float(max(costs))
+        for a, b in spans:
+            assert sum(costs[a:b]) <= total / world + cmax + 1e-9, (trial, spans)
+    assert shard.group_base(3, 5) == 15

@@ -416,3 +416,40 @@ def test_moves_follow_the_wrapping_systematic_sets():
                 period += 1
         assert r["state"].set_start == sets[period % len(sets)][0]
         assert period == r["state"].stays
+
+
+# ---------------------------------------------------------------------------
+# One step from a fixed state against its exact law: Metropolis proposes a
+# uniform bit and accepts w.p. min(1, e^{-beta Delta}); Rejection-Free moves
+# to neighbour y w.p. proportional to min(1, e^{-beta Delta_y}) (Sec. 1.2,
+# Eq. (1) with the symmetric proposal) with M = 1 + Geom(p).
+# ---------------------------------------------------------------------------
+def test_one_step_laws_from_a_fixed_state():
+    n, beta, draws = 5, 0.4, 40000
+    Q = synth.dense_int(n, -3, 3, seed=8, dtype=np.int32)
+    b = synth.vector_int(n, -3, 3, seed=8, dtype=np.int32)
+    p = O.Problem(q=Q, b=b)
+    x = np.array([1, 0, 1, 1, 0], np.uint8)
+    E = lambda v: float(v @ Q.astype(np.float64) @ v + b @ v)  # noqa: E731
+    dE = np.array([E(np.where(np.arange(n) == i, 1 - x, x)) - E(x) for i in range(n)])
+    acc = np.minimum(1.0, np.exp(-beta * dE))
+    for variant, k in (("metropolis", 1), ("rf", n)):
+        cfg = O.make_config(variant, k=k, seed=21)
+        counts = np.zeros(n + 1)  # bits, then "stayed"
+        msum = 0.0
+        for cid in range(draws):
+            st = O.ChainState(p, x, 100)
+            fl, ms = O.run_chain(p, cfg, np.float32(beta), cid, st, 1)
+            counts[fl[0] if fl[0] >= 0 else n] += 1
+            msum += ms[0]
+        if variant == "metropolis":
+            want = np.append(acc / n, 1.0 - acc.sum() / n)
+            assert msum == draws
+        else:
+            want = np.append(acc / acc.sum(), 0.0)
+            # E[M] = 1 / p, p = the mean acceptance over the n proposals
+            assert abs(msum / draws - n / acc.sum()) < 0.05 * n / acc.sum()
+        keep = want > 0
+        chi2 = (((counts[keep] - draws * want[keep]) ** 2) / (draws * want[keep])).sum()
+        assert chi2 < 25.0, (variant, counts, draws * want)  # <= 5 dof, p < 1e-4
+        assert counts[~keep].sum() == 0

@@ -453,3 +453,37 @@ def test_one_step_laws_from_a_fixed_state():
         chi2 = (((counts[keep] - draws * want[keep]) ** 2) / (draws * want[keep])).sum()
         assert chi2 < 25.0, (variant, counts, draws * want)  # <= 5 dof, p < 1e-4
         assert counts[~keep].sum() == 0
+
+
+def test_one_basic_step_against_subset_enumeration():
+    # Basic PNS (Sec. 3.2): a uniform k-subset S, then y in S w.p.
+    # w_y / sum_S w with w = min(1, e^{-beta Delta}), and M = 1 + Geom(p_S),
+    # p_S = sum_S w / k; exact law by enumerating the C(n, k) subsets
+    from itertools import combinations
+    n, k, beta, draws = 5, 2, 0.4, 40000
+    Q = synth.dense_int(n, -3, 3, seed=8, dtype=np.int32)
+    b = synth.vector_int(n, -3, 3, seed=8, dtype=np.int32)
+    p = O.Problem(q=Q, b=b)
+    x = np.array([1, 0, 1, 1, 0], np.uint8)
+    E = lambda v: float(v @ Q.astype(np.float64) @ v + b @ v)  # noqa: E731
+    w = np.minimum(1.0, np.exp(-beta * np.array(
+        [E(np.where(np.arange(n) == i, 1 - x, x)) - E(x) for i in range(n)])))
+    subsets = list(combinations(range(n), k))
+    want = np.zeros(n)
+    mean_m = 0.0
+    for S in subsets:
+        ws = w[list(S)].sum()
+        for y in S:
+            want[y] += w[y] / ws / len(subsets)
+        mean_m += (k / ws) / len(subsets)
+    cfg = O.make_config("basic", k=k, seed=33)
+    counts = np.zeros(n)
+    msum = 0.0
+    for cid in range(draws):
+        st = O.ChainState(p, x, 100)
+        fl, ms = O.run_chain(p, cfg, np.float32(beta), cid, st, 1)
+        counts[fl[0]] += 1
+        msum += ms[0]
+    chi2 = (((counts - draws * want) ** 2) / (draws * want)).sum()
+    assert chi2 < 25.0, (counts, draws * want)
+    assert abs(msum / draws - mean_m) < 0.05 * mean_m

@@ -487,3 +487,34 @@ def test_one_basic_step_against_subset_enumeration():
     chi2 = (((counts - draws * want) ** 2) / (draws * want)).sum()
     assert chi2 < 25.0, (counts, draws * want)
     assert abs(msum / draws - mean_m) < 0.05 * mean_m
+
+
+def test_one_unbiased_record_against_its_law():
+    # Algorithm 6, first record of a fresh chain (set = bits 0 .. k-1, budget
+    # L0): M = 1 + Geom(p) with p = sum_set w / k; it moves iff M <= L0, so it
+    # stays w.p. (1 - p)^L0 (recording M = L0) and otherwise jumps to y in the
+    # set w.p. proportional to w_y
+    n, k, L0, beta, draws = 6, 3, 2, 0.8, 40000
+    Q = synth.dense_int(n, -3, 3, seed=9, dtype=np.int32)
+    b = synth.vector_int(n, -3, 3, seed=9, dtype=np.int32)
+    p = O.Problem(q=Q, b=b)
+    x = np.array([0, 1, 1, 0, 1, 0], np.uint8)
+    E = lambda v: float(v @ Q.astype(np.float64) @ v + b @ v)  # noqa: E731
+    w = np.minimum(1.0, np.exp(-beta * np.array(
+        [E(np.where(np.arange(n) == i, 1 - x, x)) - E(x) for i in range(k)])))
+    pm = w.sum() / k
+    stay = (1.0 - pm) ** L0
+    want = np.append((1.0 - stay) * w / w.sum(), stay)
+    cfg = O.make_config("unbiased", k=k, subset="systematic", L0=L0, seed=5)
+    counts = np.zeros(k + 1)
+    for cid in range(draws):
+        st = O.ChainState(p, x, L0)
+        fl, ms = O.run_chain(p, cfg, np.float32(beta), cid, st, 1)
+        assert fl[0] < k
+        counts[fl[0] if fl[0] >= 0 else k] += 1
+        if fl[0] < 0:
+            assert ms[0] == L0
+        else:
+            assert 1 <= ms[0] <= L0
+    chi2 = (((counts - draws * want) ** 2) / (draws * want)).sum()
+    assert chi2 < 25.0, (counts, draws * want)

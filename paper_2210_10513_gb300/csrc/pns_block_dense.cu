@@ -40,8 +40,8 @@ int block_occupancy(int qtype, int threads, size_t smem) {
     return e == cudaSuccess ? nb : 0;
 }
 
-int32_t block_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R) {
-    const BlockSmem L = block_smem(ld, k, hbytes, qbytes, R);
+int32_t block_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R, int32_t W) {
+    const BlockSmem L = block_smem(ld, k, hbytes, qbytes, R, W);
     return round16((L.group_bytes + R - 1) / R);
 }
 

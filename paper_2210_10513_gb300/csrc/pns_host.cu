@@ -237,7 +237,7 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     const int R = pt ? c.R : 1;
     for (int64_t i = 0; i < c.chains; i += R) {
         const InstHost &ih = c.inst[chains[i].inst];
-        const int32_t per = c.blocked   ? block_chain_bytes(ih.ld, ih.k, c.hbytes, c.qtype == PNS_Q_I16 ? 2 : 4, R)
+        const int32_t per = c.blocked   ? block_chain_bytes(ih.ld, ih.k, c.hbytes, c.qtype == PNS_Q_I16 ? 2 : 4, R, c.gw)
                             : c.spec > 0 && c.sweep ? sweep_chain_bytes(ih.ld, ih.n, ih.k, c.hbytes, c.spec)
                             : c.spec > 0 ? spec_chain_bytes(ih.ld, ih.k, c.hbytes, list, c.spec)
                                          : chain_smem(ih.ld, ih.k, c.hbytes, list, c.prod > 0, slot_list).total;
@@ -312,8 +312,130 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
             pack(cap_units, out);
             return PNS_OK;
         }
-        // blocked kernel: the fewest groups per CTA at which every CTA is
-        // resident at once (else the shape with the most resident share)
+        // Blocked kernel, first choice: one CTA per SM, each holding the
+        // exchange groups of one record form (positions per lane,
+        // block_ppl), so that every SM runs a single code path: groups of
+        // different forms on one SM thrash the instruction cache.  CTAs are
+        // shared out over the forms in proportion to their groups.
+        if (const char *e = getenv("PNS_FORM_PER_SM"); !e || atoi(e)) {
+            const int S = num_sms;
+            std::vector<int> ucls(units.size());
+            int64_t ncls[3] = {0, 0, 0};
+            for (size_t i = 0; i < units.size(); ++i) {
+                const int ppl = block_ppl(c.inst[chains[units[i].first].inst].k);
+                ucls[i] = ppl == 1 ? 0 : (ppl == 2 ? 1 : 2);
+                ncls[ucls[i]] += 1;
+            }
+            int64_t m[3];
+            int64_t msum = 0;
+            for (int f = 0; f < 3; ++f) {
+                m[f] = (ncls[f] + cap_units - 1) / cap_units;
+                msum += m[f];
+            }
+            if (msum <= S) {
+                // the remaining SMs in proportion to each form's groups times
+                // a per-group weight (largest remainder), never more CTAs than
+                // groups.  The weights follow the measured time of a group's
+                // period: the wide-set form (4 positions per lane, k > 62)
+                // takes about three times as long per record as one position
+                // per lane, and runs fewer records per period.
+                const double wf[3] = {1.0, 1.5, 3.0};
+                double wsum = 0.0;
+                for (int f = 0; f < 3; ++f) wsum += wf[f] * static_cast<double>(ncls[f]);
+                const int64_t spare = S - msum;
+                int64_t give[3] = {0, 0, 0}, given = 0;
+                double rem[3];
+                for (int f = 0; f < 3; ++f) {
+                    const double want = static_cast<double>(S) * wf[f] * ncls[f] / wsum - m[f];
+                    give[f] = want > 0 ? std::min<int64_t>(static_cast<int64_t>(want), ncls[f] - m[f]) : 0;
+                    rem[f] = want > 0 ? want - give[f] : 0.0;
+                    given += give[f];
+                }
+                while (given > spare) {  // (rounding cannot overshoot, but stay safe)
+                    for (int f = 0; f < 3 && given > spare; ++f)
+                        if (give[f] > 0) give[f] -= 1, given -= 1;
+                }
+                while (given < spare) {
+                    int fb = -1;
+                    for (int f = 0; f < 3; ++f)
+                        if (m[f] + give[f] < ncls[f] && (fb < 0 || rem[f] > rem[fb])) fb = f;
+                    if (fb < 0) break;
+                    give[fb] += 1;
+                    rem[fb] -= 1.0;
+                    given += 1;
+                }
+                for (int f = 0; f < 3; ++f) m[f] += give[f];
+                // pack each form: largest group first to the least-filled CTA with room
+                std::vector<std::vector<int>> members;
+                std::vector<size_t> load;
+                bool ok = true;
+                for (int f = 0; f < 3 && ok; ++f) {
+                    const size_t b0 = members.size();
+                    for (int64_t i = 0; i < m[f]; ++i) {
+                        members.emplace_back();
+                        load.push_back(0);
+                    }
+                    for (size_t ui = 0; ui < units.size(); ++ui) {
+                        if (ucls[ui] != f) continue;
+                        const Unit &u = units[ui];
+                        int64_t best = -1;
+                        for (size_t b2 = b0; b2 < members.size(); ++b2) {
+                            if (static_cast<int>(members[b2].size()) >= cap_units || load[b2] + u.bytes > smem_cap) continue;
+                            if (best < 0 || load[b2] < load[best]) best = static_cast<int64_t>(b2);
+                        }
+                        if (best < 0) {
+                            if (static_cast<int>(members.size()) >= S) {
+                                ok = false;
+                                break;
+                            }
+                            members.emplace_back();
+                            load.push_back(0);
+                            best = static_cast<int64_t>(members.size()) - 1;
+                        }
+                        members[best].push_back(static_cast<int>(ui));
+                        load[best] += u.bytes;
+                    }
+                }
+                if (ok) {
+                    PlanOut o;
+                    o.smem_off.assign(c.chains, 0);
+                    int max_groups = 0;
+                    for (size_t b2 = 0; b2 < members.size(); ++b2) {
+                        if (members[b2].empty()) continue;
+                        CtaDesc d;
+                        d.first = static_cast<int32_t>(o.cta_chains.size());
+                        d.count = 0;
+                        d.groups = static_cast<int32_t>(members[b2].size());
+                        d.pad = 0;
+                        size_t off = 0;
+                        for (int ui : members[b2]) {
+                            const Unit &u = units[ui];
+                            const int32_t per = u.bytes / u.count;
+                            for (int s2 = 0; s2 < u.count; ++s2) {
+                                o.smem_off[u.first + s2] = static_cast<int32_t>(off) + s2 * per;
+                                o.cta_chains.push_back(u.first + s2);
+                            }
+                            off += u.bytes;
+                            d.count += u.count;
+                        }
+                        o.cta.push_back(d);
+                        o.smem = std::max(o.smem, off);
+                        max_groups = std::max(max_groups, static_cast<int>(d.groups));
+                    }
+                    // a full SM's registers per CTA keeps every CTA alone on its SM
+                    o.block = cap_units * 32 * wpg;
+                    const int occ = block_occupancy(c.qtype, o.block, o.smem);
+                    o.resident = occ >= 1 && static_cast<int>(o.cta.size()) <= S;
+                    (void)max_groups;
+                    if (o.resident) {
+                        out = o;
+                        return PNS_OK;
+                    }
+                }
+            }
+        }
+        // otherwise: the fewest groups per CTA at which every CTA is resident
+        // at once (else the shape with the most resident share)
         double best_share = -1.0;
         for (int u = 1; u <= cap_units; ++u) {
             PlanOut o;

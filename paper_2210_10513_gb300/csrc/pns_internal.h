@@ -122,26 +122,38 @@ PNS_HD ChainSmem chain_smem(int32_t ld, int32_t k, int32_t hbytes, bool list, bo
 // A chain's fields stay in global memory; shared memory holds, per chain, the
 // k fields of its current set, its bits, a log of the period's flips, its
 // ChainState and a few control words, and, per group, the k x k sub-block
-// Q[N_i, N_i], the set's b and diagonal and the group's work queue.  The host
+// Q[N_i, N_i], the set's b and diagonal, the group's work queue and one draw
+// buffer per warp (W warps).  The host
 // gives every chain of a group ceil(group_bytes / R) bytes.
 constexpr int BLOCK_LOG = 128;  // flips logged before a chain applies them itself
+// Each warp of a group keeps the random numbers of its chain's next records:
+// DRAW_BUF race exponentials (records of kp entries) and DRAW_MAXB Exp(1).
+constexpr int DRAW_BUF = 256;
+constexpr int DRAW_MAXB = 16;
+
+// Positions of the current set each lane of the period-blocked kernel holds:
+// the fewest of 1, 2 and 4 that leave lane 31 free (k <= 31 PPL), and 4 up to
+// k = 128.  Also the kernel's code path (record form) for the group.
+PNS_HD int block_ppl(int k) { return k <= 31 ? 1 : (k <= 62 ? 2 : 4); }
 
 struct BlockSmem {
-    int32_t insf, xw, log, state, scratch, chain_bytes, sub, bd, ctrl, group_bytes;
+    int32_t insf, xw, log, state, scratch, chain_bytes, sub, bd, ctrl, wbuf, group_bytes;
 };
 
-PNS_HD BlockSmem block_smem(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R) {
+PNS_HD BlockSmem block_smem(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R, int32_t W) {
     BlockSmem s;
     s.insf = 0;
-    s.xw = round16(k * hbytes);
+    s.xw = round16(((k + 3) & ~3) * hbytes);
     s.log = s.xw + round16(ld / 8);
     s.state = s.log + 4 * BLOCK_LOG;
     s.scratch = s.state + static_cast<int32_t>(sizeof(ChainState));
     s.chain_bytes = s.scratch + 32;  // log length, records, finalised flag, set start, first step
+    const int32_t kp = (k + 3) & ~3;         // sub-block row stride: 16-byte rows of 4-byte entries
     s.sub = R * s.chain_bytes;
-    s.bd = s.sub + round16(k * k * qbytes);  // b, then diag, of the set: 4-byte entries, 16-byte aligned
-    s.ctrl = s.bd + 2 * round16(4 * k);      // queue order[16], next, running, pad[2], records and slot by temperature [16] each
-    s.group_bytes = s.ctrl + 208;
+    s.bd = s.sub + round16(k * kp * qbytes);  // b, then diag, of the set: 4-byte entries, 16-byte aligned
+    s.ctrl = s.bd + 2 * round16(4 * kp);      // queue order[16], next, running, pad[2], records and slot by temperature [16] each
+    s.wbuf = s.ctrl + 208;                    // W draw buffers
+    s.group_bytes = s.wbuf + W * 4 * (DRAW_BUF + DRAW_MAXB);
     return s;
 }
 

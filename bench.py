@@ -1,15 +1,29 @@
 """Benchmark of the batched PNS sampler on one GB300 (or N, one process each).
 
-Workload (default): dense symmetric int16 QUBO, n = 1024, entries and b
-uniform in [-100, 100], beta = 0.05, 256 independent chains, Unbiased PNS with
-systematic sets of k = 64 and L0 = 100.  One bench step = one pns_run of
-`--records` jump steps (records) for every chain.  The metric is jump samples
-(records) per second over all chains; flips/s, original (Metropolis-
-equivalent) samples/s, the Basic-PNS rate and the plain one-chain-per-launch
-rate are reported beside it.
+Default workload (the headline line): batched uneven parallel tempering.
+512 fp32 QUBO instances with n uniform in [128, 2048] and Q = (A + A^T)/2,
+A i.i.d. N(0, 1), b = 0; 8 replicas per instance on the geometric beta ladder
+0.1 .. 10 (4096 chains); Unbiased PNS on systematic sets of k = max(1, n // 16)
+with L0 = 100; adjacent temperatures exchange every 100 original samples.
+One bench step = one pns_run of `--samples` (default 10,000) original samples
+for every chain, i.e. 100 exchange rounds.  The metric is jump samples
+(records) per second over all chains; flips/s and original (Metropolis-
+equivalent) samples/s are reported beside it, and the roofline counts one
+fp32 row of Q (4 n bytes) per flip against the measured HBM copy bandwidth.
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
-the host cores instead (bounded sample of the same workload).
+The line also carries the end-to-end rate through the public API (instances
+copied in from pinned host memory, create + run + read per step), the CPU
+oracle timed on the host cores (`cpu_baseline`), the one-group-per-launch
+form (`batched_over_plain`) and, unless `--quick`, the dense int16 n = 1024
+workload's figures with its L2-side roofline (`dense1024`).
+
+With torchrun (N > 1) the instances are sharded across ranks by n^2 (whole
+exchange groups, no data-path collective); the value is the records of all
+ranks over the slowest rank's time.
+
+`--impl reference` times the CPU oracle instead (a bounded sample of the same
+workload on the host cores).  `--workload dense1024|lattice|fit|donuts` prints
+the other benchmark shapes.
 """
 import argparse
 import json
@@ -25,6 +39,13 @@ sys.path.insert(0, ROOT)
 
 from paper_2210_10513_gb300 import synth  # noqa: E402
 
+# ---- tempering workload ---------------------------------------------------------
+T_INST = 512
+T_REPLICAS = 8
+T_L0 = 100
+T_SWAP = 100
+
+# ---- dense int16 workload -----------------------------------------------------------
 N = 1024
 K = 64
 CHAINS = 256
@@ -39,18 +60,87 @@ def workload(seed):
     return q, b
 
 
-def config_desc(records, l2):
-    return {"workload": "dense int16 QUBO n=1024, 256 chains, Unbiased PNS k=64 L0=100, beta=0.05, "
-                        "%d records per chain per step" % records,
-            "n": N, "k": K, "chains": CHAINS, "beta": BETA, "L0": L0, "variant": "unbiased-systematic",
-            "records_per_step": records, "l2": l2, "parallelism": "independent chains"}
+def tempering_ladder():
+    return synth.geometric_ladder(0.1, 10.0, T_REPLICAS)
+
+
+def tempering_desc(n_inst, samples):
+    return ("parallel tempering: %d fp32 QUBO instances n~U[128,2048], Q=(A+A^T)/2 A~N(0,1), b=0, %d replicas on "
+            "beta 0.1..10 (%d chains), Unbiased PNS k=n//16 L0=100, exchange every 100 original samples; %d original "
+            "samples per chain per step" % (n_inst, T_REPLICAS, n_inst * T_REPLICAS, samples))
+
+
+def tempering_config(n_inst, samples, world=1):
+    return {"workload": tempering_desc(n_inst, samples), "instances": n_inst, "replicas": T_REPLICAS,
+            "chains": n_inst * T_REPLICAS, "L0": T_L0, "swap_interval": T_SWAP, "samples_per_step": samples,
+            "l2": "Q (3 GB) exceeds L2; a 256 MiB buffer is also written between timed steps",
+            "parallelism": "instances sharded by n^2 over %d rank(s)" % world}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def _oracle_worker(args):
+def _oracle_tempering_worker(args):
+    seed, inst_ids, n_inst, warm, samples = args
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    ns = synth.tempering_sizes(n_inst, seed)
+    ladder = tempering_ladder()
+    recs = flips = 0
+    summ = 0.0
+    busy = 0.0
+    for p in inst_ids:
+        n = ns[p]
+        prob = O.Problem(q=synth.tempering_q(p, n, seed))
+        cfg = dict(variant="unbiased", k=max(1, n // 16), L0=T_L0, seed=seed)
+        x0s = [np.zeros(n, np.uint8)] * T_REPLICAS
+        # warm-up rounds, then the timed rounds continue the same chains
+        res = O.run_tempering(prob, ladder, cfg, p, p * T_REPLICAS, x0s, warm // T_SWAP, 1, tape=False) if warm else None
+        if res is not None:
+            x0s = [r["x"] for r in res]
+        t0 = time.perf_counter()
+        res = O.run_tempering(prob, ladder, cfg, p, p * T_REPLICAS, x0s, samples // T_SWAP, 1, tape=False)
+        busy += time.perf_counter() - t0
+        recs += sum(int(r["state"].step) for r in res)
+        flips += sum(int(r["state"].flips) for r in res)
+        summ += sum(float(r["state"].sum_m) for r in res)
+    return recs, flips, summ, busy
+
+
+def oracle_tempering_rate(n_inst, every, warm, samples, seed=0):
+    """The oracle as it stands on all host cores (spawned workers), on every
+    `every`-th exchange group of the workload: `warm` original samples of
+    warm-up (untimed), then `samples` timed.  The rate is the sample's
+    records over the summed busy time divided by the workers."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ids = list(range(0, n_inst, every))
+    workers = min(cores, len(ids))
+    parts = [ids[i::workers] for i in range(workers)]
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
+        list(pool.map(_oracle_tempering_worker, [(seed, [0], n_inst, 0, T_SWAP)] * workers, timeout=600))
+        t0 = time.perf_counter()
+        res = list(pool.map(_oracle_tempering_worker, [(seed, p, n_inst, warm, samples) for p in parts], timeout=3000))
+        wall = time.perf_counter() - t0
+    recs = sum(r[0] for r in res)
+    flips = sum(r[1] for r in res)
+    summ = sum(r[2] for r in res)
+    busy = max(r[3] for r in res)  # the slowest worker's timed part
+    single = float(np.mean([r[0] / r[3] for r in res if r[3] > 0]))
+    return dict(rate=recs / busy, flips_rate=flips / busy, orig_rate=summ / busy, wall=wall, busy=busy, cores=workers,
+                single_core_rate=single,
+                sample="%d of the %d exchange groups (every %d-th instance, 8 replicas each): %d original samples of "
+                       "warm-up, then %d timed" % (len(ids), n_inst, every, warm, samples))
+
+
+def _oracle_dense_worker(args):
     seed, chain_ids, records, variant = args
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
@@ -59,68 +149,53 @@ def _oracle_worker(args):
     cfg = O.make_config(variant, k=K, L0=L0, seed=seed)
     t0 = time.perf_counter()
     tot = 0
-    flips = 0
-    summ = 0.0
     for cid in chain_ids:
         st = O.ChainState(prob, np.zeros(N, np.uint8), L0)
         O.run_chain(prob, cfg, np.float32(BETA), cid, st, records, tape=False)
         tot += records
-        flips += st.st.flips
-        summ += st.st.sum_m
-    return tot, flips, summ, time.perf_counter() - t0
+    return tot, time.perf_counter() - t0
 
 
-def oracle_rate(records, chains_sample, seed=0, variant="unbiased"):
-    """Time the oracle as it stands on all host cores (spawned workers)."""
+def oracle_dense_rate(records, chains_sample, seed=0, variant="unbiased"):
     import concurrent.futures as cf
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     workers = min(cores, chains_sample)
     ids = list(range(chains_sample))
     parts = [ids[i::workers] for i in range(workers)]
-    # spawned workers (never forked after CUDA initialisation); a dead worker
-    # raises BrokenProcessPool instead of hanging
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
-        list(pool.map(_oracle_worker, [(seed, [0], 10, variant)] * workers, timeout=600))  # load the library
+        list(pool.map(_oracle_dense_worker, [(seed, [0], 10, variant)] * workers, timeout=600))
         t0 = time.perf_counter()
-        res = list(pool.map(_oracle_worker, [(seed, p, records, variant) for p in parts], timeout=1200))
+        res = list(pool.map(_oracle_dense_worker, [(seed, p, records, variant) for p in parts], timeout=1200))
         wall = time.perf_counter() - t0
     tot = sum(r[0] for r in res)
-    flips = sum(r[1] for r in res)
-    summ = sum(r[2] for r in res)
-    # one core's rate: each worker runs its chains serially on one core
-    single = float(np.mean([r[0] / r[3] for r in res]))
-    return dict(rate=tot / wall, flips_rate=flips / wall, orig_rate=summ / wall, wall=wall, cores=workers,
-                single_core_rate=single,
-                sample="%d chains x %d records of the same workload (chains 0..%d)" % (chains_sample, records,
-                                                                                      chains_sample - 1))
+    return dict(rate=tot / wall, cores=workers, single_core_rate=float(np.mean([r[0] / r[1] for r in res])),
+                sample="%d chains x %d records of the dense int16 n=1024 workload" % (chains_sample, records))
 
 
 def reference_arm(args):
+    """The CPU oracle, as it stands, on the tempering workload (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import build_oracle
     build_oracle.build()
-    cores = os.cpu_count() or 1
-    chains_sample = min(CHAINS, cores)
-    records = 100000
+    every, warm, samples = 4, 1000, 5000
     for _ in range(args.warmup):
-        oracle_rate(2000, chains_sample)
-    times = []
-    rates = []
+        oracle_tempering_rate(args.instances, 64, 0, T_SWAP)
+    rates, times = [], []
     last = None
     for _ in range(args.steps):
-        r = oracle_rate(records, chains_sample)
-        times.append(r["wall"])
+        r = oracle_tempering_rate(args.instances, every, warm, samples)
         rates.append(r["rate"])
+        times.append(r["busy"])
         last = r
     value = float(np.mean(rates))
     line = {"impl": "reference", "metric": "PNS jump samples/s (records/s)", "value": value, "unit": "samples/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean(times) * 1e3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": config_desc(args.records, "flushed between timed steps (256 MiB write)"),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": tempering_config(args.instances, args.samples),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"], "single_core_value": last["single_core_rate"]},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -128,7 +203,7 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
-# GPU arm
+# Clock sampling
 # ---------------------------------------------------------------------------
 
 class Clocks:
@@ -183,11 +258,12 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def gpu_arm(args):
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def _dist_setup():
     import torch
-
-    from paper_2210_10513_gb300 import pns
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -196,166 +272,247 @@ def gpu_arm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local, dist
+
+
+def _allreduce(dist, vals, op="sum"):
+    if dist is None:
+        return vals
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
+def tempering_arm(args):
+    """The headline: the tempering workload, sharded by instance over ranks."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns, shard
+
+    world, rank, local, dist = _dist_setup()
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)  # non-default stream: pns_run replays a captured CUDA graph
     torch.cuda.set_stream(stream)
-    seed = args.seed + rank  # weak scaling: each rank samples its own independent chains
-    q, b = workload(args.seed)
-    qd = torch.from_numpy(q).to(dev)
-    bd = torch.from_numpy(b).to(dev)
-    records = args.records
+    n_inst = args.instances
+    samples = args.samples
+    ns_all = synth.tempering_sizes(n_inst, args.seed)
+    lo, hi = shard.shard_instances([n * n * T_REPLICAS for n in ns_all], world, rank)
+    ladder = tempering_ladder()
+    cb = shard.chain_base([T_REPLICAS] * n_inst, 1, lo)
+    gb = shard.group_base(1, lo)
+    qs = [synth.tempering_q(p, ns_all[p], args.seed) for p in range(lo, hi)]
+    ns = ns_all[lo:hi]
 
-    def make(variant, **kw):
-        opts = dict(graph=True, autotune=not args.no_autotune)
+    def make(q_list, **kw):
+        plist = [dict(n=n, q=q, betas=ladder, k=max(1, n // 16)) for n, q in zip(ns, q_list)]
+        opts = dict(variant="unbiased", k=1, chains_per_replica=1, L0=T_L0, swap_interval=T_SWAP, seed=args.seed,
+                    tape=False, chain_base=cb, group_base=gb)
         opts.update(kw)
-        return pns.Sampler([dict(n=N, q=qd, b=bd, betas=[BETA])], variant=variant, k=K, chains_per_replica=CHAINS,
-                           L0=L0, seed=seed, tape=False, **opts)
+        return pns.Sampler(plist, **opts)
 
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-
-    def timed(sampler, steps, warmup, plain=False, recs=None):
-        recs = recs or records
-        for _ in range(warmup):
-            (sampler.run_plain if plain else sampler.run)(recs)
-        torch.cuda.synchronize()
-        before = sampler.read(tape=False)["stats"]
-        ms = []
-        for _ in range(steps):
+    qd = [torch.from_numpy(q).to(dev) for q in qs]
+    s = make(qd, graph=True, autotune=not args.no_autotune)
+    row_bytes = np.repeat(4 * np.asarray(ns, dtype=np.float64), T_REPLICAS)  # one fp32 row per flip, per chain
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2 (Q itself is 3 GB)
+    for _ in range(args.warmup):
+        s.run(samples)
+    torch.cuda.synchronize()
+    before = s.read(tape=False)["stats"]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank), local)
+    ms = []
+    with clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            (sampler.run_plain if plain else sampler.run)(recs)
+            s.run(samples)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        after = sampler.read(tape=False)["stats"]
-        d = {k: float(after[k].sum() - before[k].sum()) for k in ("steps", "flips", "sum_m", "saturated")}
-        return ms, d
-
-    s_unb = make("unbiased")
-    # main timed region, barrier + sync on both sides, clocks sampled during it
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank), local)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with clk:
-        t0 = time.perf_counter()
-        ms, d = timed(s_unb, args.steps, args.warmup)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if dist is not None:
         dist.barrier()
+    after = s.read(tape=False)["stats"]
+    info = s.info
+    d = {k: (after[k] - before[k]).astype(np.float64) for k in ("steps", "flips", "sum_m", "saturated", "swaps_accepted")}
     kernel_s = sum(ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([kernel_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        kernel_s = float(t.item())
-        tot = torch.tensor([d["steps"], d["flips"], d["sum_m"], d["saturated"]], dtype=torch.float64, device=dev)
-        dist.all_reduce(tot)
-        d = dict(steps=float(tot[0]), flips=float(tot[1]), sum_m=float(tot[2]), saturated=float(tot[3]))
-    value = d["steps"] / kernel_s
-    extra = {}
-    if rank == 0 and not args.quick:
-        # Basic PNS (fresh random 64-subset every step), same workload
-        s_basic = make("basic")
-        ms_b, d_b = timed(s_basic, max(3, args.steps // 2), 2)
-        extra["basic_samples_per_s"] = d_b["steps"] / (sum(ms_b) / 1e3)
-        s_basic.close()
-        # plain form: one chain per launch, launches back to back
-        s_plain = make("unbiased", chains_per_cta=1, graph=False, autotune=False)
-        plain_records = max(100, records // 10)
-        ms_p, d_p = timed(s_plain, 1, 1, plain=True, recs=plain_records)
-        extra["plain_samples_per_s"] = d_p["steps"] / (sum(ms_p) / 1e3)
-        extra["batched_over_plain"] = value / extra["plain_samples_per_s"]
-        extra["plain_records_per_chain"] = plain_records
-        s_plain.close()
-    info = s_unb.info
-    s_unb.close()
+    byts = float((d["flips"] * row_bytes).sum())
+    tot = _allreduce(dist, [d["steps"].sum(), d["flips"].sum(), d["sum_m"].sum(), d["saturated"].sum(), byts,
+                            d["swaps_accepted"].sum()])
+    kmax = _allreduce(dist, [kernel_s], "max")[0]
+    records, flips, summ, sat, byts_all, swaps = tot
+    value = records / kmax
 
-    # e2e: pinned host buffers through the public API, copies inside the timed region
-    e2e = None
-    if rank == 0:
-        q_host = torch.from_numpy(q.copy()).pin_memory()
-        b_host = torch.from_numpy(b.copy()).pin_memory()
-        e_steps = max(2, min(args.steps, 5))
-        h2d = q.nbytes + b.nbytes + 4
-        t_e = []
-        recs = 0
-        d2h = 0
-        for i in range(e_steps + 1):
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            s = pns.Sampler([dict(n=N, q=q_host, b=b_host, betas=[BETA])], variant="unbiased", k=K,
-                            chains_per_replica=CHAINS, L0=L0, seed=seed + 1000 + i, tape=False)
-            s.run(records)
-            out = s.read(tape=False)
-            s.close()
-            t2 = time.perf_counter()
-            if i > 0:  # first one warms the allocator
-                t_e.append(t2 - t1)
-                recs += int(out["stats"]["steps"].sum())
-                d2h = out["states"].nbytes + out["stats"].nbytes
-        e2e = {"value": recs / sum(t_e), "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+    extra = {}
+    if rank == 0 and not args.quick and world == 1:
+        # one exchange group per launch, launches back to back: the form
+        # that runs one group at a time (records are the same)
+        sp = make(qd, chains_per_cta=1)
+        p_samples = 10 * T_SWAP
+        sp.run_plain(p_samples)
+        torch.cuda.synchronize()
+        b0 = sp.read(tape=False)["stats"]["steps"].sum()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sp.run_plain(p_samples)
+        e1.record(stream)
+        e1.synchronize()
+        p_recs = float(sp.read(tape=False)["stats"]["steps"].sum() - b0)
+        extra["plain_samples_per_s"] = p_recs / (e0.elapsed_time(e1) / 1e3)
+        extra["batched_over_plain"] = value / extra["plain_samples_per_s"]
+        extra["plain_form"] = "one exchange group per launch, %d launches back to back, %d original samples" % (
+            sp.info.ctas, p_samples)
+        sp.close()
+    s.close()
+    del qd
+
+    # e2e: the instances from pinned host memory through the public API;
+    # create + run + read (states and statistics) per step
+    q_host = [torch.from_numpy(q).pin_memory() for q in qs]
+    h2d = int(sum(q.nbytes for q in qs) + 4 * T_REPLICAS * len(qs))
+    e_steps = max(2, min(args.steps, 4))
+    t_e, recs_e, d2h = [], 0.0, 0
+    for i in range(e_steps + 1):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        se = make(q_host, seed=args.seed + 1000 + i)
+        se.run(samples)
+        out = se.read(tape=False)
+        se.close()
+        t2 = time.perf_counter()
+        if i > 0:  # the first one warms the allocator and the module
+            t_e.append(t2 - t1)
+            recs_e += float(out["stats"]["steps"].sum())
+            d2h = int(out["states"].nbytes + out["stats"].nbytes)
+    e_tot = _allreduce(dist, [recs_e])[0]
+    e_time = _allreduce(dist, [sum(t_e)], "max")[0]
+    e2e = {"value": e_tot / e_time, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": e_time / len(t_e) * 1e3}
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    hbm = peaks.get("hbm_gbs")
-    peak_note = "measured"
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_note = "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
     if hbm is None:
-        hbm = 6800.0
-        peak_note = "fallback"
-    flips_per_launch = d["flips"] / max(1, args.steps) / max(1, world)
-    avg_launch_s = kernel_s / max(1, args.steps)
-    achieved = flips_per_launch * ROW_BYTES / avg_launch_s / 1e9
-    # DRAM bytes per launch from one ncu capture of the kernel this mapping
-    # runs (null when the capture was of another kernel)
+        hbm, peak_note = 6800.0, "fallback"
+    avg_launch = kernel_s / max(1, args.steps)
+    achieved = byts / max(1, args.steps) / avg_launch / 1e9  # rank 0's kernel
     traffic = None
-    kernel = "pns_sweep_kernel" if info.set_sweep else ("pns_spec_kernel" if info.spec_depth else "pns_sample_kernel")
-    tr_path = os.path.join(ROOT, "profiles", "traffic_dense_int16_n1024.json")
+    tr_path = os.path.join(ROOT, "profiles", "traffic_tempering.json")
     if os.path.exists(tr_path):
         tr = json.load(open(tr_path))
-        if tr.get("kernel", "").startswith(kernel):
+        if tr.get("kernel", "").startswith("pns_block_kernel") and tr.get("samples") == samples and \
+                tr.get("instances") == n_inst and tr.get("source_sha") == _kernel_sha():
             traffic = tr.get("dram_bytes_per_launch")
     cpu = None
     if world == 1 and not args.no_cpu:
         from oracle import build_oracle
         build_oracle.build()
-        cores = os.cpu_count() or 1
-        r = oracle_rate(100000, min(CHAINS, cores))
+        r = oracle_tempering_rate(n_inst, 4, 1000, 5000, args.seed)
         cpu = {"value": r["rate"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
                "single_core_value": r["single_core_rate"]}
     line = {
         "metric": "PNS jump samples/s (records/s)",
-        "value": value * 1.0, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": kernel_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": config_desc(records, "flushed between timed steps (256 MiB write)"),
-        "flips_per_s": d["flips"] / kernel_s, "original_samples_per_s": d["sum_m"] / kernel_s,
-        "saturated_moves": int(d["saturated"]),
+        "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": kmax * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": tempering_config(n_inst, samples, world),
+        "flips_per_s": flips / kmax, "original_samples_per_s": summ / kmax, "saturated_moves": int(sat),
+        "swaps_accepted": int(swaps),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "peak_kind": peak_note,
-                     "algorithmic_bytes": "2048 B (one int16 row of Q) per flip"},
+                     "algorithmic_bytes": "4 n bytes (one fp32 row of Q) per flip, summed over the launch's flips"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
         "clocks": clk.summary(), "wall_s": wall,
-        "mapping": {"warps_per_chain": info.warps_per_chain, "team_warps": info.team_warps,
-                    "producer_warps": info.producer_warps, "spec_depth": info.spec_depth,
-                    "set_sweep": info.set_sweep, "ctas": info.ctas,
-                    "autotune": not args.no_autotune,
-                    "cuda_graph": True},
+        "mapping": {"period_blocked": info.period_blocked, "team_warps": info.team_warps, "ctas": info.ctas,
+                    "autotune": not args.no_autotune, "cuda_graph": True},
     }
     line.update(extra)
+    if not args.quick and world == 1:
+        line["dense1024"] = dense1024_figures(args, stream)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _kernel_sha():
+    """Hash of the sources of the period-blocked kernel: a stored ncu traffic
+    figure is used only for the kernel it was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pns_block.cuh", "pns_block_dense.cu", "pns_sampler.cuh", "pns_device.cuh", "pns_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2210_10513_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dense1024_figures(args, stream, records=10000, steps=10, warmup=3):
+    """The dense int16 n = 1024 workload (256 chains, Unbiased k = 64, beta =
+    0.05): records/s and its roofline on the L2 side (Q, 2 MiB, stays in L2)
+    against the library's measured L2 read bandwidth."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    dev = torch.device("cuda", torch.cuda.current_device())
+    q, b = workload(args.seed)
+    qd, bd = torch.from_numpy(q).to(dev), torch.from_numpy(b).to(dev)
+    s = pns.Sampler([dict(n=N, q=qd, b=bd, betas=[BETA])], variant="unbiased", k=K, chains_per_replica=CHAINS, L0=L0,
+                    seed=args.seed, tape=False, graph=True, autotune=not args.no_autotune)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        s.run(records)
+    torch.cuda.synchronize()
+    before = s.read(tape=False)["stats"]
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.run(records)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    after = s.read(tape=False)["stats"]
+    info = s.info
+    s.close()
+    secs = sum(ms) / 1e3
+    recs = float(after["steps"].sum() - before["steps"].sum())
+    flips = float(after["flips"].sum() - before["flips"].sum())
+    l2 = pns.pns_l2_read_probe(64 << 20, 50, stream.cuda_stream)
+    achieved = flips / steps * ROW_BYTES / (secs / steps) / 1e9
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    return {"workload": "dense int16 QUBO n=1024, 256 chains, Unbiased PNS k=64 L0=100, beta=0.05, %d records per "
+                        "chain per step" % records,
+            "value": recs / secs, "unit": "samples/s", "flips_per_s": flips / secs, "ms_per_step": secs * 1e3 / steps,
+            "roofline_l2": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                            "peak_kind": "measured (pns_l2_read_probe: 64 MiB resident buffer read by every SM)",
+                            "algorithmic_bytes": "2048 B (one int16 row of Q) per flip"},
+            "roofline_hbm_frac": achieved / hbm,
+            "mapping": {"set_sweep": info.set_sweep, "spec_depth": info.spec_depth, "ctas": info.ctas}}
+
+
+def dense1024_arm(args):
+    """`--workload dense1024`: the dense int16 workload's own line."""
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    fig = dense1024_figures(args, stream, records=args.records, steps=args.steps, warmup=args.warmup)
+    fig.update({"metric": "PNS jump samples/s (records/s)", "workload": "dense1024", "steps": args.steps,
+                "warmup": args.warmup})
+    print(json.dumps(fig), flush=True)
 
 
 def fit_workload(args):
@@ -480,10 +637,6 @@ def donuts_workload(args):
 
 def side_workload(args):
     """Other benchmark shapes, one JSON line each (not the headline):
-    tempering -- 512 fp32 instances, n uniform in [128, 2048], 8 replicas on a
-                 geometric beta ladder 0.1..10, Unbiased PNS k = n // 16,
-                 exchange every L0 = 100 original samples; one step = 1000
-                 original samples (10 exchange rounds) for every chain.
     lattice   -- 256 x 256 periodic +-1 lattice (n = 65536) as CSR, 64 chains
                  for each beta in {0.2, 0.44, 1.0}, Unbiased k = 1024; one step
                  = `--records` records for every chain."""
@@ -495,20 +648,7 @@ def side_workload(args):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     tune = dict(graph=True, autotune=not args.no_autotune)
-    if args.workload == "tempering":
-        n_inst = args.instances
-        probs, ladder = synth.workload_tempering(n_inst, seed=args.seed)
-        plist = []
-        for pr in probs:
-            plist.append(dict(n=pr["n"], q=torch.from_numpy(pr["q"]).to(dev), betas=ladder, k=max(1, pr["n"] // 16)))
-        s = pns.Sampler(plist, variant="unbiased", k=1, chains_per_replica=1, L0=100, swap_interval=100,
-                        seed=args.seed, tape=False, **tune)
-        per_step = 1000
-        ns = np.repeat(np.array([pr["n"] for pr in probs]), len(ladder))
-        row_bytes = 4 * ns
-        desc = ("tempering: %d fp32 instances n~U[128,2048], 8 replicas (beta 0.1..10), Unbiased k=n/16, "
-                "swap every 100 original samples, 1000 original samples per chain per step" % n_inst)
-    elif args.workload == "donuts":
+    if args.workload == "donuts":
         return donuts_workload(args)
     elif args.workload == "fit":
         return fit_workload(args)
@@ -568,25 +708,28 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--records", type=int, default=10000)
+    ap.add_argument("--samples", type=int, default=10000, help="tempering: original samples per chain per step")
+    ap.add_argument("--records", type=int, default=10000, help="dense1024 / lattice / fit / donuts: records per step")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="heuristic chain-to-CTA mapping")
-    ap.add_argument("--quick", action="store_true", help="skip the Basic / plain side measurements")
-    ap.add_argument("--workload", default="dense1024", choices=["dense1024", "tempering", "lattice", "fit", "donuts"])
-    ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--quick", action="store_true", help="skip the plain-form and dense1024 side measurements")
+    ap.add_argument("--workload", default="tempering", choices=["tempering", "dense1024", "lattice", "fit", "donuts"])
+    ap.add_argument("--instances", type=int, default=T_INST)
     args = ap.parse_args()
-    if args.workload != "dense1024":
-        from paper_2210_10513_gb300 import build as B
-        B.build()
-        side_workload(args)
-        return
+    if args.samples % T_SWAP != 0:
+        ap.error("--samples must be a multiple of %d" % T_SWAP)
     if args.impl == "reference":
         reference_arm(args)
+        return
+    from paper_2210_10513_gb300 import build as B
+    B.build()
+    if args.workload == "tempering":
+        tempering_arm(args)
+    elif args.workload == "dense1024":
+        dense1024_arm(args)
     else:
-        from paper_2210_10513_gb300 import build as B
-        B.build()
-        gpu_arm(args)
+        side_workload(args)
 
 
 if __name__ == "__main__":

@@ -304,6 +304,15 @@ typedef struct {
 pns_status pns_donuts_run(const pns_donuts_config *cfg, int64_t chains, int64_t steps, const float *x0,
                           pns_donuts_stats *stats, void *stream);
 
+/* Read bandwidth (GB/s, written to *gbs) that the current device sustains
+ * from a buffer of `bytes` (>= 1 MiB, a multiple of 16; pick one well inside
+ * L2, e.g. 64 MiB on GB300) read `passes` times by every SM after a warm-up
+ * read, timed with CUDA events on `stream`.  A measurement aid for roofline
+ * denominators (the L2 side of a kernel whose working set stays in L2); the
+ * paper has no counterpart.  Allocates and frees its own buffer and
+ * synchronises `stream`. */
+pns_status pns_l2_read_probe(size_t bytes, int32_t passes, double *gbs, void *stream);
+
 /* Size of the fixed device array that pns_sample_static works in.  Every GPU
  * that loads this library holds it until the process exits. */
 #define PNS_STATIC_SCRATCH_BYTES (16u << 20)

@@ -73,7 +73,7 @@ assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
 
 EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_read_samples", "pns_moments",
            "pns_energy_grads", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore", "pns_destroy",
-           "pns_last_error", "pns_sample_static", "pns_read_best", "pns_donuts_run")
+           "pns_last_error", "pns_sample_static", "pns_read_best", "pns_donuts_run", "pns_l2_read_probe")
 STATIC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
@@ -108,6 +108,8 @@ def lib():
         L.pns_read_best.restype = C.c_int
         L.pns_donuts_run.argtypes = [vp, C.c_int64, C.c_int64, vp, vp, vp]
         L.pns_donuts_run.restype = C.c_int
+        L.pns_l2_read_probe.argtypes = [C.c_size_t, C.c_int32, C.POINTER(C.c_double), vp]
+        L.pns_l2_read_probe.restype = C.c_int
         L.pns_destroy.argtypes = [vp]
         L.pns_destroy.restype = None
         L.pns_last_error.argtypes = []
@@ -284,6 +286,13 @@ def pns_checkpoint(ctx):
 def pns_restore(ctx, buf):
     buf = np.ascontiguousarray(buf, dtype=np.uint8)
     _check(lib().pns_restore(ctx, _addr(buf), buf.nbytes))
+
+
+def pns_l2_read_probe(nbytes=64 << 20, passes=50, stream=None):
+    """GB/s read from a buffer resident in L2 (pns_l2_read_probe)."""
+    out = C.c_double(0.0)
+    _check(lib().pns_l2_read_probe(nbytes, passes, C.byref(out), _stream(stream)))
+    return out.value
 
 
 def pns_destroy(ctx):

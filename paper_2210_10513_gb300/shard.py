@@ -11,20 +11,30 @@ on the host side of torch.distributed.
 
 def shard_instances(costs, world, rank):
     """Contiguous [start, stop) of instances for `rank`, balancing the summed
-    cost (e.g. n^2 bytes of Q per instance times its chains)."""
+    cost (e.g. n^2 bytes of Q per instance times its chains).  Boundary b
+    (b = 1 .. world - 1) sits at the instance edge nearest the cost target
+    b * total / world, kept strictly increasing so that no rank is empty while
+    there are at least `world` instances; the last rank ends at the last
+    instance."""
     n = len(costs)
     if world <= 1:
         return 0, n
-    total = float(sum(costs))
+    prefix = [0.0]
+    for c in costs:
+        prefix.append(prefix[-1] + float(c))
+    total = prefix[-1]
     bounds = [0]
-    acc = 0.0
-    target = total / world
-    for i, c in enumerate(costs):
-        acc += c
-        while len(bounds) < world and acc >= target * len(bounds) and i + 1 < n:
-            bounds.append(i + 1)
-    while len(bounds) < world:
-        bounds.append(n)
+    for b in range(1, world):
+        target = total * b / world
+        # the edge i (0 < i < n) whose prefix cost is nearest the target
+        best = None
+        for i in range(1, n):
+            if best is None or abs(prefix[i] - target) < abs(prefix[best] - target):
+                best = i
+        best = best if best is not None else n
+        lo = bounds[-1] + 1 if n >= world else bounds[-1]  # at least one instance per rank
+        hi = n - (world - b) if n >= world else n           # and room for the ranks after it
+        bounds.append(min(max(best, lo), max(lo, hi)))
     bounds.append(n)
     return bounds[rank], bounds[rank + 1]
 

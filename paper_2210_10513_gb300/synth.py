@@ -135,15 +135,24 @@ def workload_dense_int1024(seed=0, n=1024):
                 beta=0.05, chains=256, k=64)
 
 
+def tempering_sizes(n_instances=512, seed=0, n_lo=128, n_hi=2048):
+    """n of each instance of the tempering workload: uniform in [n_lo, n_hi]."""
+    g = _rng(seed, 99)
+    return [int(n) for n in g.integers(n_lo, n_hi + 1, size=n_instances)]
+
+
+def tempering_q(p, n, seed=0):
+    """Q of instance p of the tempering workload: (A + A^T)/2, A N(0, 1) fp32
+    (drawn on its own stream, so that any subset of instances can be made)."""
+    return dense_normal(int(n), 1.0, seed, stream=1000 + p)
+
+
 def workload_tempering(n_instances=512, seed=0, n_lo=128, n_hi=2048, replicas=8):
     """Instances with n uniform in [n_lo, n_hi], Q = (A + A^T)/2 with A
     N(0, 1) fp32, b = 0, geometric beta ladder 0.1 .. 10 with `replicas`
     rungs, k = max(1, n // 16)."""
-    g = _rng(seed, 99)
-    ns = g.integers(n_lo, n_hi + 1, size=n_instances)
-    probs = []
-    for p, n in enumerate(ns):
-        probs.append(dict(q=dense_normal(int(n), 1.0, seed, stream=1000 + p), b=None, n=int(n)))
+    ns = tempering_sizes(n_instances, seed, n_lo, n_hi)
+    probs = [dict(q=tempering_q(p, n, seed), b=None, n=n) for p, n in enumerate(ns)]
     return probs, geometric_ladder(0.1, 10.0, replicas)
 
 

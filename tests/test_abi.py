@@ -26,7 +26,7 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = set(re.findall(r"\b(pns_[a-z_]+)\s*\(", text))
+    names = set(re.findall(r"\b(pns_[a-z0-9_]+)\s*\(", text))
     return sorted(names)
 
 

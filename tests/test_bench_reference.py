@@ -22,4 +22,5 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert 0 < cb["single_core_value"] <= cb["value"] * 1.5
     assert d["e2e"] == {"value": d["value"], "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"].startswith("dense int16 QUBO n=1024")
+    assert d["config"]["workload"].startswith("parallel tempering: 512 fp32 QUBO instances")
+    assert d["config"]["instances"] == 512 and d["config"]["replicas"] == 8 and d["dtype"] == "f32"

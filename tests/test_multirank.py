@@ -61,6 +61,14 @@ def _free_port():
     return port
 
 
+def test_shard_bounds_place_each_edge_nearest_its_target():
+    # costs [1, 10] on two ranks: the edge after the first instance is nearer
+    # the half-way cost (5.5) than the end, so neither rank is empty
+    assert [shard.shard_instances([1, 10], 2, r) for r in range(2)] == [(0, 1), (1, 2)]
+    assert [shard.shard_instances([10, 1], 2, r) for r in range(2)] == [(0, 1), (1, 2)]
+    assert [shard.shard_instances([3, 3, 3, 3], 2, r) for r in range(2)] == [(0, 2), (2, 4)]
+
+
 def test_shard_bounds_cover_everything():
     costs = [5, 1, 1, 9, 2, 2, 7]
     for world in (1, 2, 3, 4, 7, 9):
@@ -101,6 +109,8 @@ def test_shard_costs_balanced():
         owned = np.zeros(n, int)
         for a, b in spans:
             owned[a:b] += 1
+            if n >= world:
+                assert b > a, (trial, spans)  # no rank left without an instance
         assert (owned == 1).all()
         total, cmax = float(sum(costs)), float(max(costs))
         for a, b in spans:

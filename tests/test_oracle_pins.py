@@ -188,6 +188,35 @@ def test_multiplicity_law():
     assert (ms >= 1).all() and (ms == np.floor(ms)).all()
 
 
+@pytest.mark.parametrize("deltas,beta", [([7], 1.0), ([14, 15, 17], 1.0)])
+def test_multiplicity_law_small_p(deltas, beta):
+    """M = 1 + Geom(p) (Sec. 1.2) where moves are rare: p near 1e-3 and 4e-7,
+    the range Basic PNS and RF reach on the headline instance.  The oracle
+    forms M = floor(E1 / -ln(1 - p)) + 1 in fp32; the law of M must still be
+    the geometric one: mean 1/p, and P(M <= m) = 1 - (1 - p)^m at three m."""
+    d = np.array(deltas, dtype=np.int64)
+    k = len(deltas)
+    p_exact = float(np.mean(np.exp(-beta * d)))
+    N = 200000
+    ms = np.empty(N)
+    p = None
+    for s in range(N):
+        _, _, p, m, sat = O.decide(d, k, beta, 7, 3, s)
+        ms[s] = m
+        assert sat == 0
+    # the fp32 p the oracle uses, against the closed form (det_expf <= 2 ulp,
+    # the quantised weight sum <= k 2^-32 relative)
+    assert p == pytest.approx(p_exact, rel=1e-6)
+    p = float(p)
+    se = math.sqrt((1 - p) / p**2 / N)
+    assert abs(ms.mean() - 1 / p) < 5 * se
+    for frac in (0.1, 0.7, 2.0):
+        mq = math.floor(frac / p)
+        F = 1.0 - (1.0 - p) ** mq
+        assert abs((ms <= mq).mean() - F) < 5 * math.sqrt(F * (1 - F) / N), (frac, mq)
+    assert (ms >= 1).all() and (ms == np.floor(ms)).all()
+
+
 def test_multiplicity_edges():
     # all neighbours downhill: p = 1 and M = 1 (Example 1: Geom(1) gives E[M] = 1)
     _, _, p, m, sat = O.decide(np.array([-5, -1, 0], np.int64), 3, 1.0, 0, 0, 0)

@@ -310,10 +310,13 @@ def run_independent(problems, betas, cfg_kwargs, chains_per_replica, x0, n_recor
 
 def run_tempering(problem, betas, cfg_kwargs, group_id, chain_id0, x0s, rounds, periods_per_round, tape=True,
                   max_records_per_period=None):
-    """Parallel tempering for one group of R replicas of Unbiased PNS: each
-    round every replica runs `periods_per_round` complete periods, then one
-    swap round.  Returns per-slot tapes and states."""
+    """Parallel tempering for one group of R replicas: each round every
+    replica runs `periods_per_round` units, then one swap round.  Unbiased PNS
+    (Algorithm 6): a unit is one complete period of L0 original samples.
+    Metropolis (Algorithm 1): a unit is one record, i.e. one original sample.
+    Returns per-slot tapes and states."""
     cfg = make_config(**cfg_kwargs)
+    metropolis = cfg_kwargs.get("variant") == "metropolis"
     R = len(betas)
     states = [ChainState(problem, x0s[s], cfg.L0, beta_idx=s) for s in range(R)]
     tapes = [([], []) for _ in range(R)]
@@ -323,8 +326,11 @@ def run_tempering(problem, betas, cfg_kwargs, group_id, chain_id0, x0s, rounds, 
         for s in range(R):
             st = states[s]
             beta = float(betas32[st.st.beta_idx])
-            fl, ms = run_chain(problem, cfg, beta, chain_id0 + s, st, cap * periods_per_round,
-                               stop_after_periods=periods_per_round, tape=True)
+            if metropolis:
+                fl, ms = run_chain(problem, cfg, beta, chain_id0 + s, st, periods_per_round, tape=True)
+            else:
+                fl, ms = run_chain(problem, cfg, beta, chain_id0 + s, st, cap * periods_per_round,
+                                   stop_after_periods=periods_per_round, tape=True)
             if tape:
                 tapes[s][0].append(fl)
                 tapes[s][1].append(ms)

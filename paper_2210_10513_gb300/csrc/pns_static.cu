@@ -57,8 +57,9 @@ pns_status sfail(pns_status st, const char *fmt, ...) {
 size_t up256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
 
 // The device address of the scratch array on the current device, resolved
-// once per device with that device current.
-pns_status scratch_address(void **out) {
+// once per device with that device current (and again after a call on that
+// device failed, so that an address from a torn-down context is not reused).
+pns_status scratch_address(int *dev_out, void **out) {
     int dev = -1;
     SCU(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return sfail(PNS_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
@@ -68,9 +69,21 @@ pns_status scratch_address(void **out) {
         SCU(cudaGetSymbolAddress(&p, g_pns_static_scratch));
         g_scratch_addr[dev] = p;
     }
+    *dev_out = dev;
     *out = g_scratch_addr[dev];
     return PNS_OK;
 }
+
+// Forgets the device's cached address unless the call completed.
+struct ForgetOnFailure {
+    int dev = -1;
+    bool done = false;
+    ~ForgetOnFailure() {
+        if (done || dev < 0) return;
+        std::lock_guard<std::mutex> lock(g_mutex);
+        g_scratch_addr[dev] = nullptr;
+    }
+};
 
 // Fills the chain / CTA descriptors and the initial chain states for one
 // instance: chains_per_cta consecutive chains per CTA, slot = c mod R.
@@ -144,6 +157,31 @@ extern "C" {
 pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int64_t steps, uint32_t *states,
                              double *multiplicities, int32_t *flips, pns_stats *stats, void *stream) {
     if (!prob || !cfg) return sfail(PNS_ERR_INVALID_ARG, "prob and cfg are required");
+    // the configuration fields pns_create checks, with its messages
+    const int wpc = cfg->warps_per_chain;
+    if (!(wpc == 0 || wpc == 1 || wpc == 2 || wpc == 4 || wpc == 8 || wpc == 16 || wpc == 32))
+        return sfail(PNS_ERR_INVALID_ARG, "warps_per_chain must be 0, 1, 2, 4, 8, 16 or 32");
+    if (cfg->tape < 0 || cfg->tape > 2) return sfail(PNS_ERR_INVALID_ARG, "tape must be 0, 1 or 2");
+    if (cfg->graph != 0 && cfg->graph != 1) return sfail(PNS_ERR_INVALID_ARG, "graph must be 0 or 1");
+    if (cfg->autotune != 0 && cfg->autotune != 1) return sfail(PNS_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (cfg->track_best != 0 && cfg->track_best != 1) return sfail(PNS_ERR_INVALID_ARG, "track_best must be 0 or 1");
+    if (cfg->chains_per_cta < 0 || cfg->reserved != 0 || cfg->chain_base < 0 || cfg->group_base < 0)
+        return sfail(PNS_ERR_INVALID_ARG, "chains_per_cta, chain_base, group_base must be >= 0 and reserved 0");
+    if (prob->k < 0 || prob->reserved != 0) return sfail(PNS_ERR_INVALID_ARG, "problem: k < 0 or reserved != 0");
+    // what this entry point does not do
+    if (cfg->track_best) return sfail(PNS_ERR_UNSUPPORTED, "pns_sample_static keeps no best states (track_best)");
+    if (cfg->tape == 2) return sfail(PNS_ERR_UNSUPPORTED, "pns_sample_static writes no sample tape (tape = 2)");
+    if ((multiplicities != nullptr) != (flips != nullptr))
+        return sfail(PNS_ERR_INVALID_ARG, "pass both tape outputs (multiplicities and flips) or neither");
+    if (cfg->tape == 1 && !multiplicities)
+        return sfail(PNS_ERR_INVALID_ARG, "tape = 1 needs the multiplicities and flips outputs");
+    {
+        // it synchronises `stream`, which a stream capture does not allow
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        SCU(cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return sfail(PNS_ERR_UNSUPPORTED, "pns_sample_static synchronises its stream: not under stream capture");
+    }
     const int n = prob->n;
     if (prob->fmt != PNS_DENSE) return sfail(PNS_ERR_UNSUPPORTED, "pns_sample_static takes a dense instance");
     if (n < 32 || n % 32 != 0) return sfail(PNS_ERR_INVALID_ARG, "n = %d must be a positive multiple of 32", n);
@@ -202,7 +240,8 @@ pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int
                      kScratchBytes);
 
     void *base_v = nullptr;
-    pns_status st = scratch_address(&base_v);
+    ForgetOnFailure forget;
+    pns_status st = scratch_address(&forget.dev, &base_v);
     if (st != PNS_OK) return st;
     unsigned char *base = static_cast<unsigned char *>(base_v);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -222,8 +261,22 @@ pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int
     SCU(cudaStreamSynchronize(s));
     if (chk.flags & FLAG_NONFINITE) return sfail(PNS_ERR_RANGE, "non-finite entry");
     if (chk.flags & FLAG_ASYM) return sfail(PNS_ERR_NOT_SYMMETRIC, "Q is not symmetric");
-    if (qt != PNS_Q_F32 && static_cast<long long>(chk.bound) > 715827882LL)
+    if (qt == PNS_Q_F32) {
+        double v;
+        memcpy(&v, &chk.bound, sizeof(double));
+        if (!(v < 1e30)) return sfail(PNS_ERR_RANGE, "field bound %g too large for fp32 fields", v);
+    } else if (static_cast<long long>(chk.bound) > 715827882LL) {
         return sfail(PNS_ERR_RANGE, "3 * field bound reaches 2^31");
+    }
+    // the temperatures, as pns_create checks them (copied through a small host buffer)
+    for (int r0 = 0; r0 < R; r0 += 64) {
+        float bh[64];
+        const int m = std::min(64, R - r0);
+        SCU(cudaMemcpyAsync(bh, prob->betas + r0, sizeof(float) * m, cudaMemcpyDeviceToHost, s));
+        SCU(cudaStreamSynchronize(s));
+        for (int i = 0; i < m; ++i)
+            if (!(bh[i] >= 0.0f) || !(bh[i] < 3.0e38f)) return sfail(PNS_ERR_INVALID_ARG, "betas must be finite and >= 0");
+    }
 
     InstDesc in;
     in.q = prob->q;
@@ -273,7 +326,7 @@ pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int
     P.pt = 0;
     P.tape = (flips && multiplicities) ? 1 : 0;
     P.prod = 0;
-    P.chain_base = static_cast<uint32_t>(cfg->chain_base > 0 ? cfg->chain_base : 0);
+    P.chain_base = static_cast<uint32_t>(cfg->chain_base);
     if (steps > 0)
         SCU(launch_sampler(PNS_DENSE, qt, 4, T, P, static_cast<int>(ctas), per_cta * 32 * T,
                            static_cast<size_t>(per_cta) * chain_bytes, s));
@@ -288,6 +341,7 @@ pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int
         SCU(cudaMemcpyAsync(stats, d_stats, sizeof(pns_stats) * chains, cudaMemcpyDefault, s));
     }
     SCU(cudaStreamSynchronize(s));
+    forget.done = true;
     if (code != 0) return sfail(static_cast<pns_status>(code), "device reported error %d", code);
     return PNS_OK;
 }

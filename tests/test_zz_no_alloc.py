@@ -89,3 +89,76 @@ def test_static_rejects_sizes_beyond_the_array():
         pns.pns_sample_static(p, c, 10)
     assert ei.value.status == 3 and "scratch" in str(ei.value)
     assert C.sizeof(C.c_char * pns.STATIC_SCRATCH_BYTES) == 16 << 20
+
+
+def _static_problem(n=64, q=None, betas=(0.5,)):
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    q = q if q is not None else synth.dense_int(n, -20, 20, 1, np.int32)
+    qd = torch.from_numpy(q).cuda()
+    bt = torch.tensor(np.asarray(betas, np.float32)).cuda()
+    keep = [qd, bt]
+    p = pns.make_problem(n, q=qd, betas=[0.0] * len(betas), keep=keep)
+    p.betas = bt.data_ptr()
+    return p, keep
+
+
+def test_static_rejects_what_create_rejects():
+    """The inputs pns_create turns away get the same status here: a negative
+    or non-finite beta, an fp32 entry whose field bound overflows fp32
+    fields, one tape output without the other, and options this entry point
+    does not carry out."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    for betas in ([-0.5], [float("inf")], [0.3, float("nan")]):
+        p, keep = _static_problem(betas=betas)
+        with pytest.raises(pns.PnsError) as ei:
+            pns.pns_sample_static(p, pns.make_config("unbiased", k=4), 10)
+        assert ei.value.status == 1 and "betas" in str(ei.value)
+    big = np.zeros((64, 64), np.float32)
+    big[3, 5] = big[5, 3] = 3.0e38  # finite, but a row sum past 1e30
+    p, keep = _static_problem(q=big)
+    with pytest.raises(pns.PnsError) as ei:
+        pns.pns_sample_static(p, pns.make_config("unbiased", k=4), 10)
+    assert ei.value.status == 3
+    p, keep = _static_problem()
+    m = torch.zeros((1, 10), dtype=torch.float64, device="cuda")
+    with pytest.raises(pns.PnsError) as ei:
+        pns.pns_sample_static(p, pns.make_config("unbiased", k=4), 10, multiplicities=m)
+    assert ei.value.status == 1
+    for kw, status in ((dict(track_best=True), 8), (dict(tape=2), 8), (dict(chain_base=-1), 1)):
+        with pytest.raises(pns.PnsError) as ei:
+            pns.pns_sample_static(p, pns.make_config("unbiased", k=4, **kw), 10)
+        assert ei.value.status == status, kw
+    # the same problem with valid options still runs
+    stats = np.zeros(1, pns.STATS_DTYPE)
+    pns.pns_sample_static(p, pns.make_config("unbiased", k=4, seed=2), 50, stats=stats)
+    assert stats["steps"][0] == 50
+
+
+def test_static_refuses_a_capturing_stream():
+    """It synchronises its stream, so under stream capture it must return
+    PNS_ERR_UNSUPPORTED and leave the caller's capture valid."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    p, keep = _static_problem()
+    s = torch.cuda.Stream()
+    x = torch.zeros(4, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            pns.pns_sample_static(p, pns.make_config("unbiased", k=4), 10, stream=s)
+        except pns.PnsError as e:
+            err = e
+        x.add_(1.0)
+        g.capture_end()
+    assert err is not None and err.status == 8
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 4.0

@@ -236,6 +236,15 @@ pns_status pns_energy_grads(int32_t n, float beta, const pns_moment_scalars *sca
                             const double *data_xx, double data_mean_energy, double *dQ, double *db, double *dbeta,
                             void *stream);
 
+/* The data term of the Boltzmann log-likelihood's energy (Sec. 8 target
+ * pi ~ exp(-beta E)): the mean energy of data with moments data_x (n) and
+ * data_xx (n x n), <E>_D = sum_ij data_xx_ij Q_ij + sum_i data_x_i b_i, in
+ * fp64 with a fixed reduction order, written to *out.  q (n x n fp32), b (n
+ * fp32, NULL = 0), data_x (required with b), data_xx and out are device
+ * memory; asynchronous on `stream`. */
+pns_status pns_data_energy(int32_t n, const float *q, const float *b, const double *data_x, const double *data_xx,
+                           double *out, void *stream);
+
 /* Copies the maintained local fields h (chains x field_stride elements of
  * field_bytes each, integers or fp32 per pns_info) to `out`. */
 pns_status pns_fields(pns_ctx *ctx, void *out, void *stream);
@@ -330,16 +339,22 @@ pns_status pns_l2_read_probe(size_t bytes, int32_t passes, double *gbs, void *st
  *     (swap_interval = 0); cfg->x0, when given, in device memory; the
  *     producer warp is not used.
  *   - outputs: states (chains x n/32 words, host or device), multiplicities
- *     and flips (device, chains x steps, both or neither), stats (host or
- *     device, chains entries); any may be NULL.
- *   - results equal pns_create + pns_run + pns_read on the same inputs.
+ *     and flips (device, chains x steps, both or neither: one alone is
+ *     PNS_ERR_INVALID_ARG), stats (host or device, chains entries); any may
+ *     be NULL.
+ *   - results equal pns_create + pns_run + pns_read on the same inputs, and
+ *     inputs that pns_create rejects are rejected with the same status
+ *     (configuration fields, symmetry, finiteness, field range, betas);
+ *     track_best = 1 and tape = 2 return PNS_ERR_UNSUPPORTED.
  *   - sizes whose working memory exceeds the array return PNS_ERR_RANGE with
  *     the bytes needed; no partial work is done.
  *   - the first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current), and so does the next call after a failed one.
+ *   - it synchronises `stream`, so it cannot run while `stream` is being
+ *     captured into a CUDA graph: such a call returns PNS_ERR_UNSUPPORTED and
+ *     leaves the capture intact.
  *   - every call shares the array and leaves its contents behind; each call
- *     resets what it reads.  Calls that overlap on the GPU race on the array.
- *   - synchronises `stream` before returning. */
+ *     resets what it reads.  Calls that overlap on the GPU race on the array. */
 pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int64_t steps, uint32_t *states,
                              double *multiplicities, int32_t *flips, pns_stats *stats, void *stream);
 

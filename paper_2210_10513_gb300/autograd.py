@@ -2,8 +2,9 @@
 
 The forward passes run the CUDA sampler (Unbiased PNS by default) with the
 sample tape on and reduce the tape to multiplicity-weighted moments on the
-tensor cores (pns_moments); the backward passes assemble the gradients in a
-CUDA kernel (pns_energy_grads).  This module only marshals tensors.
+tensor cores (pns_moments); the data energy of the fit (pns_data_energy) and
+the gradients (pns_energy_grads) are CUDA kernels too.  This module only
+marshals tensors.
 
 MeanEnergy(Q, b, beta) -> <E>, the multiplicity-weighted mean of
     E(x) = x^T Q x + b^T x under pi(x) ~ exp(-beta E(x)).  Its gradients are
@@ -69,7 +70,12 @@ class BoltzmannFit(torch.autograd.Function):
     @staticmethod
     def forward(ctx, Q, b, beta, data_x, data_xx, steps=2000, sampler_kw=None):
         mom = _run_moments(Q, b, float(beta), sampler_kw, steps)
-        data_E = float((data_xx.double() * Q.double()).sum() + (data_x.double() * b.double()).sum())
+        out = torch.empty(1, dtype=torch.float64, device=Q.device)
+        q32 = Q.detach().to(torch.float32).contiguous()
+        b32 = b.detach().to(torch.float32).contiguous() if b is not None else None
+        dx = data_x.detach().to(torch.float64).contiguous()
+        pns.pns_data_energy(Q.shape[0], q32, b32, dx, data_xx.detach().to(torch.float64).contiguous(), out)
+        data_E = float(out.item())
         ctx.n = Q.shape[0]
         ctx.beta = float(beta)
         ctx.mom = mom

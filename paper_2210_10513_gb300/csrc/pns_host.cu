@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +37,40 @@ pns_status fail(pns_status st, const char *fmt, ...) {
                 return fail(PNS_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_));                 \
             return fail(PNS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                    \
         }                                                                                          \
+    } while (0)
+
+// Host-side fault injection for failure-path tests (environment variable
+// PNS_FAULT, read at each call): "alloc" makes every device allocation of the
+// library fail with PNS_ERR_OOM, "alloc_after=N" every allocation after the
+// first N made since PNS_FAULT took its current value, and "launch" makes
+// pns_run / pns_run_plain fail with PNS_ERR_CUDA before launching.  Nothing
+// reaches the GPU; the call returns as the real failure would.
+bool fault_injected(const char *what) {
+    const char *e = getenv("PNS_FAULT");
+    return e && strstr(e, what);
+}
+
+bool alloc_fault() {
+    static std::mutex mu;
+    static std::string seen;
+    static long long allocs = 0;
+    const char *e = getenv("PNS_FAULT");
+    std::lock_guard<std::mutex> lock(mu);
+    const std::string now = e ? e : "";
+    if (now != seen) {  // a new setting: count from zero
+        seen = now;
+        allocs = 0;
+    }
+    const long long done = allocs++;
+    if (!e) return false;
+    if (const char *a = strstr(e, "alloc_after=")) return done >= atoll(a + 12);
+    return strstr(e, "alloc") != nullptr;
+}
+
+#define CU_MALLOC(ptr, bytes)                                                                      \
+    do {                                                                                           \
+        if (alloc_fault()) return fail(PNS_ERR_OOM, "injected allocation failure (PNS_FAULT)");    \
+        CU(cudaMalloc(ptr, bytes));                                                                \
     } while (0)
 
 int qtype_bytes(int qtype) { return qtype == PNS_Q_I16 ? 2 : 4; }
@@ -657,11 +692,11 @@ static pns_status apply_mapping(pns_ctx *c, Mapping m, cudaStream_t s) {
     c->n_cta = static_cast<int>(pl.cta.size());
     c->n_threads = pl.block;
     c->smem = pl.smem;
-    CU(cudaMalloc(&c->d_chain, sizeof(ChainDesc) * chains.size()));
+    CU_MALLOC(&c->d_chain, sizeof(ChainDesc) * chains.size());
     CU(cudaMemcpyAsync(c->d_chain, chains.data(), sizeof(ChainDesc) * chains.size(), cudaMemcpyHostToDevice, s));
-    CU(cudaMalloc(&c->d_cta, sizeof(CtaDesc) * pl.cta.size()));
+    CU_MALLOC(&c->d_cta, sizeof(CtaDesc) * pl.cta.size());
     CU(cudaMemcpyAsync(c->d_cta, pl.cta.data(), sizeof(CtaDesc) * pl.cta.size(), cudaMemcpyHostToDevice, s));
-    CU(cudaMalloc(&c->d_cta_chains, sizeof(int32_t) * pl.cta_chains.size()));
+    CU_MALLOC(&c->d_cta_chains, sizeof(int32_t) * pl.cta_chains.size());
     CU(cudaMemcpyAsync(c->d_cta_chains, pl.cta_chains.data(), sizeof(int32_t) * pl.cta_chains.size(),
                        cudaMemcpyHostToDevice, s));
     CU(cudaStreamSynchronize(s));
@@ -753,7 +788,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
     const size_t b_state = sizeof(ChainState) * c->chains, b_x = sizeof(uint32_t) * c->W * c->chains,
                  b_f = static_cast<size_t>(c->hbytes) * c->LD * c->chains, b_all = b_state + b_x + b_f;
     void *snap = nullptr;
-    CU(cudaMalloc(&snap, 2 * b_all));
+    CU_MALLOC(&snap, 2 * b_all);
     struct FreeSnap {
         void *p;
         ~FreeSnap() { cudaFree(p); }
@@ -907,17 +942,17 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
 
     // ---- upload ---------------------------------------------------------------
     const size_t q_bytes = static_cast<size_t>(std::max<int64_t>(q_elems, 1)) * (c->fmt == PNS_DENSE ? qb : vb);
-    CU(cudaMalloc(&c->d_q, q_bytes));
+    CU_MALLOC(&c->d_q, q_bytes);
     c->q_bytes = q_bytes;
     CU(cudaMemsetAsync(c->d_q, 0, q_bytes, s));
-    CU(cudaMalloc(&c->d_diag, static_cast<size_t>(vec_elems) * vb));
-    CU(cudaMalloc(&c->d_b, static_cast<size_t>(vec_elems) * vb));
+    CU_MALLOC(&c->d_diag, static_cast<size_t>(vec_elems) * vb);
+    CU_MALLOC(&c->d_b, static_cast<size_t>(vec_elems) * vb);
     CU(cudaMemsetAsync(c->d_diag, 0, static_cast<size_t>(vec_elems) * vb, s));
     CU(cudaMemsetAsync(c->d_b, 0, static_cast<size_t>(vec_elems) * vb, s));
-    CU(cudaMalloc(&c->d_betas, static_cast<size_t>(beta_elems) * sizeof(float)));
+    CU_MALLOC(&c->d_betas, static_cast<size_t>(beta_elems) * sizeof(float));
     if (c->fmt == PNS_CSR) {
-        CU(cudaMalloc(&c->d_rowptr, static_cast<size_t>(rp_elems) * sizeof(int32_t)));
-        CU(cudaMalloc(&c->d_col, static_cast<size_t>(std::max<int64_t>(q_elems, 1)) * sizeof(int32_t)));
+        CU_MALLOC(&c->d_rowptr, static_cast<size_t>(rp_elems) * sizeof(int32_t));
+        CU_MALLOC(&c->d_col, static_cast<size_t>(std::max<int64_t>(q_elems, 1)) * sizeof(int32_t));
     }
     int32_t *d_flags = nullptr;
     unsigned long long *d_bound = nullptr;
@@ -930,8 +965,8 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
             if (*t) cudaFree(*t);
         }
     } tmpfree{reinterpret_cast<void **>(&d_flags), reinterpret_cast<void **>(&d_bound), &d_tmp};
-    CU(cudaMalloc(&d_flags, sizeof(int32_t) * n_probs));
-    CU(cudaMalloc(&d_bound, sizeof(unsigned long long) * n_probs));
+    CU_MALLOC(&d_flags, sizeof(int32_t) * n_probs);
+    CU_MALLOC(&d_bound, sizeof(unsigned long long) * n_probs);
     CU(cudaMemsetAsync(d_flags, 0, sizeof(int32_t) * n_probs, s));
     CU(cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long) * n_probs, s));
     int64_t max_n = 0, max_nnz = 0;
@@ -941,7 +976,7 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     }
     // scratch for raw b / diag / CSR values of one instance at a time
     const size_t tmp_bytes = static_cast<size_t>(std::max<int64_t>({2 * max_n, max_nnz, 1})) * 4 + 64;
-    CU(cudaMalloc(&d_tmp, tmp_bytes));
+    CU_MALLOC(&d_tmp, tmp_bytes);
     char *tmp = static_cast<char *>(d_tmp);
     for (int p = 0; p < n_probs; ++p) {
         const pns_problem &pr = probs[p];
@@ -1030,7 +1065,7 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
         d.k = ih.k;
         d.R = ih.R;
     }
-    CU(cudaMalloc(&c->d_inst, sizeof(InstDesc) * n_probs));
+    CU_MALLOC(&c->d_inst, sizeof(InstDesc) * n_probs);
     CU(cudaMemcpyAsync(c->d_inst, idesc.data(), sizeof(InstDesc) * n_probs, cudaMemcpyHostToDevice, s));
 
     // ---- chains -------------------------------------------------------------------
@@ -1065,10 +1100,10 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     if (st != PNS_OK) return st;
 
     // ---- chain state ------------------------------------------------------------------
-    CU(cudaMalloc(&c->d_state, sizeof(ChainState) * c->chains));
-    CU(cudaMalloc(&c->d_x, sizeof(uint32_t) * c->W * c->chains));
-    CU(cudaMalloc(&c->d_fields, static_cast<size_t>(c->hbytes) * c->LD * c->chains));
-    CU(cudaMalloc(&c->d_status, sizeof(int32_t)));
+    CU_MALLOC(&c->d_state, sizeof(ChainState) * c->chains);
+    CU_MALLOC(&c->d_x, sizeof(uint32_t) * c->W * c->chains);
+    CU_MALLOC(&c->d_fields, static_cast<size_t>(c->hbytes) * c->LD * c->chains);
+    CU_MALLOC(&c->d_status, sizeof(int32_t));
     CU(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), s));
     std::vector<uint32_t> x(static_cast<size_t>(c->W) * c->chains, 0u);
     if (cfg->x0) {
@@ -1129,8 +1164,8 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
             desc[i] = d;
         }
         if (total > 0) {
-            CU(cudaMalloc(&c->d_wtab, sizeof(float4) * total));
-            CU(cudaMalloc(&c->d_wtab_desc, sizeof(int2) * c->chains));
+            CU_MALLOC(&c->d_wtab, sizeof(float4) * total);
+            CU_MALLOC(&c->d_wtab_desc, sizeof(int2) * c->chains);
             CU(cudaMemcpyAsync(c->d_wtab_desc, desc.data(), sizeof(int2) * c->chains, cudaMemcpyHostToDevice, s));
             for (const auto &e : seen)
                 if (e.second.y > 0) {
@@ -1143,7 +1178,7 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     }
     if (cfg->track_best) {
         // X_max starts as the initial state (Algorithms 8-10)
-        CU(cudaMalloc(&c->d_xbest, sizeof(uint32_t) * c->W * c->chains));
+        CU_MALLOC(&c->d_xbest, sizeof(uint32_t) * c->W * c->chains);
         CU(cudaMemcpyAsync(c->d_xbest, c->d_x, sizeof(uint32_t) * c->W * c->chains, cudaMemcpyDeviceToDevice, s));
     }
     CU(cudaStreamSynchronize(s));
@@ -1182,11 +1217,11 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
             c->d_tape_x = nullptr;
             c->d_tape_E = nullptr;
             c->tape_alloc = 0;
-            CU(cudaMalloc(&c->d_tape_flip, sizeof(int32_t) * cap * c->chains));
-            CU(cudaMalloc(&c->d_tape_m, sizeof(double) * cap * c->chains));
+            CU_MALLOC(&c->d_tape_flip, sizeof(int32_t) * cap * c->chains);
+            CU_MALLOC(&c->d_tape_m, sizeof(double) * cap * c->chains);
             if (c->cfg.tape == 2) {
-                CU(cudaMalloc(&c->d_tape_x, sizeof(uint32_t) * c->W * cap * c->chains));
-                CU(cudaMalloc(&c->d_tape_E, sizeof(double) * cap * c->chains));
+                CU_MALLOC(&c->d_tape_x, sizeof(uint32_t) * c->W * cap * c->chains);
+                CU_MALLOC(&c->d_tape_E, sizeof(double) * cap * c->chains);
             }
             c->tape_alloc = cap;
             if (c->gexec) {
@@ -1232,6 +1267,10 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.wtab_desc = c->d_wtab_desc;
     P.prefetch = (c->cfg.variant == PNS_UNBIASED && c->q_bytes > (64ull << 20)) ? 1 : 0;
     if (const char *e = getenv("PNS_PREFETCH")) P.prefetch = atoi(e) ? 1 : 0;
+    // a host-set cap on the draws of a random k-subset (tests make the bounded
+    // loop give up with it); read at each run, baked into a graph when captured
+    if (const char *e = getenv("PNS_DRAW_CAP")) P.draw_cap = static_cast<uint32_t>(strtoul(e, nullptr, 10));
+    if (fault_injected("launch")) return fail(PNS_ERR_CUDA, "injected launch failure (PNS_FAULT)");
     P.chain_base = static_cast<uint32_t>(c->cfg.chain_base);
     P.group_base = static_cast<uint32_t>(c->cfg.group_base);
     auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {
@@ -1395,10 +1434,10 @@ pns_status pns_moments(pns_ctx *c, int32_t instance, int32_t beta_idx, pns_momen
             if (*c) cudaFree(*c);
         }
     } fr{reinterpret_cast<void **>(&d_ids), &d_scratch, reinterpret_cast<void **>(&d_out)};
-    CU(cudaMalloc(&d_ids, sizeof(int32_t) * ids.size()));
-    CU(cudaMalloc(&d_scratch, scratch_bytes));
+    CU_MALLOC(&d_ids, sizeof(int32_t) * ids.size());
+    CU_MALLOC(&d_scratch, scratch_bytes);
     const size_t out_elems = 4 + 2 * static_cast<size_t>(n) + 2 * static_cast<size_t>(n) * n;
-    CU(cudaMalloc(&d_out, sizeof(double) * out_elems));
+    CU_MALLOC(&d_out, sizeof(double) * out_elems);
     CU(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, s));
     double *o_sc = d_out, *o_x = d_out + 4, *o_xx = o_x + n, *o_ex = o_xx + n * n, *o_exx = o_ex + n;
     CU(launch_moments(c->d_tape_x, c->d_tape_m, c->d_tape_E, d_ids, static_cast<int64_t>(ids.size()), c->tape_cap,
@@ -1424,6 +1463,13 @@ pns_status pns_energy_grads(int32_t n, float beta, const pns_moment_scalars *sca
     if (data_xx && !data_x) return fail(PNS_ERR_INVALID_ARG, "data_x is required with data_xx");
     CU(launch_grads(n, beta, reinterpret_cast<const double *>(scalars), mean_x, mean_xx, cov_ex, cov_exx, data_x,
                     data_xx, data_mean_energy, dQ, db, dbeta, static_cast<cudaStream_t>(stream)));
+    return PNS_OK;
+}
+
+pns_status pns_data_energy(int32_t n, const float *q, const float *b, const double *data_x, const double *data_xx,
+                           double *out, void *stream) {
+    if (n < 1 || !q || !data_xx || !out || (b && !data_x)) return fail(PNS_ERR_INVALID_ARG, "missing argument");
+    CU(launch_data_energy(n, q, b, data_x, data_xx, out, static_cast<cudaStream_t>(stream)));
     return PNS_OK;
 }
 

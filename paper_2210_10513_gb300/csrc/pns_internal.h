@@ -91,6 +91,8 @@ struct KParams {
     int32_t gw;             // period-blocked kernel: warps per exchange group
     const float4 *wtab;     // integer Q: weight tables e^{-beta d}, d = 0, 1, ... (w, its two quantised parts)
     const int2 *wtab_desc;  // per chain: (first entry, entries); entries 0 = no table
+    uint32_t draw_cap;      // 0, or the most draws a random k-subset may take (host-set, for tests)
+    uint32_t pad2;
 };
 
 PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }

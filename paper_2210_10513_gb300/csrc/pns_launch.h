@@ -78,6 +78,10 @@ cudaError_t launch_grads(int n, float beta, const double *scalars, const double 
                          const double *cov_ex, const double *cov_exx, const double *data_x, const double *data_xx,
                          double data_E, double *dQ, double *db, double *dbeta, cudaStream_t s);
 
+// Mean energy of data moments under (Q, b), fp64, deterministic.
+cudaError_t launch_data_energy(int n, const float *q, const float *b, const double *data_x, const double *data_xx,
+                               double *out, cudaStream_t s);
+
 // Sets the message pns_last_error() returns on this thread.
 void set_last_error(const char *msg);
 

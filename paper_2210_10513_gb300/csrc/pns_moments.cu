@@ -493,6 +493,32 @@ cudaError_t launch_moments(const uint32_t *tape_x, const double *tape_m, const d
     return cudaGetLastError();
 }
 
+// Mean energy of data with moments data_x, data_xx under (Q, b):
+// sum_ij data_xx_ij Q_ij + sum_i data_x_i b_i in fp64, one block, a fixed
+// reduction order (deterministic).
+__global__ void __launch_bounds__(256) data_energy_kernel(int n, const float *q, const float *b, const double *data_x,
+                                                          const double *data_xx, double *out) {
+    __shared__ double part[256];
+    double acc = 0.0;
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) acc = fma(data_xx[i], static_cast<double>(q[i]), acc);
+    if (b)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) acc = fma(data_x[i], static_cast<double>(b[i]), acc);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
+cudaError_t launch_data_energy(int n, const float *q, const float *b, const double *data_x, const double *data_xx,
+                               double *out, cudaStream_t s) {
+    data_energy_kernel<<<1, 256, 0, s>>>(n, q, b, data_x, data_xx, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_grads(int n, float beta, const double *scalars, const double *mean_x, const double *mean_xx,
                          const double *cov_ex, const double *cov_exx, const double *data_x, const double *data_xx,
                          double data_E, double *dQ, double *db, double *dbeta, cudaStream_t s) {

@@ -230,12 +230,16 @@ __device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anc
 }
 
 // First k distinct values of v_m = floor(word_m n / 2^32), m = 0, 1, ...,
-// drawn by one warp into `list`.  Returns false when the draw cap is hit.
+// drawn by one warp into `list`.  Returns false when the draw cap is hit:
+// 64 n + 1024 draws, or `cap_limit` when that is smaller and nonzero (a
+// host-set limit that lets tests make this bounded loop give up).
 __device__ __forceinline__ bool draw_subset_warp(uint64_t seed, uint32_t chain, uint64_t sstep, int n, int k,
-                                                 int ld, int32_t *list, uint32_t *bitmap, int lane) {
+                                                 int ld, int32_t *list, uint32_t *bitmap, int lane,
+                                                 uint32_t cap_limit = 0u) {
     for (int w = lane; w < ld / 32; w += 32) bitmap[w] = 0u;
     __syncwarp();
-    const uint32_t cap = 64u * static_cast<uint32_t>(n) + 1024u;
+    uint32_t cap = 64u * static_cast<uint32_t>(n) + 1024u;
+    if (cap_limit != 0u && cap_limit < cap) cap = cap_limit;
     int got = 0;
     uint32_t m0 = 0;
     while (got < k) {
@@ -254,7 +258,14 @@ __device__ __forceinline__ bool draw_subset_warp(uint64_t seed, uint32_t chain, 
         got += __popc(bal);
         m0 += 32;
         __syncwarp();
-        if (got < k && m0 >= cap) return false;
+        if (got < k && m0 >= cap) {
+            // give up, leaving every list entry a valid bit index (a kernel
+            // that evaluates the record before it checks the status reads
+            // only in-range fields)
+            for (int t = got + lane; t < k; t += 32) list[t] = 0;
+            __syncwarp();
+            return false;
+        }
     }
     return true;
 }
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
         }
         if (slot_list && wit == TC + prod - 1) {
             int32_t *sl = reinterpret_cast<int32_t *>(slot + 16 + 4 * k);
-            const bool ok = draw_subset_warp(seed, chain_id, step, n, k, ld, sl, bitmap, lane);
+            const bool ok = draw_subset_warp(seed, chain_id, step, n, k, ld, sl, bitmap, lane, P.draw_cap);
             if (lane == 0) reinterpret_cast<int32_t *>(slot)[3] = ok ? 0 : 1;
         }
     };
@@ -568,7 +579,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                         dead = 1;
                     }
                 } else {
-                    if (wit == 0 && !draw_subset_warp(seed, chain_id, step, n, k, ld, list, bitmap, lane)) {
+                    if (wit == 0 && !draw_subset_warp(seed, chain_id, step, n, k, ld, list, bitmap, lane, P.draw_cap)) {
                         if (lane == 0) {
                             set_status(P.status, ST_TIMEOUT);
                             *dead_slot = 1;
@@ -580,7 +591,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             } else if (use_list && !list_valid) {
                 if (wit == 0 &&
                     !draw_subset_warp(seed, chain_id, static_cast<uint64_t>(st.period_start), n, k, ld, list, bitmap,
-                                      lane)) {
+                                      lane, P.draw_cap)) {
                     if (lane == 0) {
                         set_status(P.status, ST_TIMEOUT);
                         *dead_slot = 1;

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(32 * D <= 512 ? 512 : 1024) pns_spec_kernel(co
                     uint32_t *bm = reinterpret_cast<uint32_t *>(base + L.bitmaps + buf * L.bitmap_bytes);
                     if (!(w == 0 && list_valid)) {
                         const uint64_t ps = w == 0 ? static_cast<uint64_t>(st.period_start) : step;
-                        if (!draw_subset_warp(seed, chain_id, ps, n, k, ld, lb, bm, lane)) {
+                        if (!draw_subset_warp(seed, chain_id, ps, n, k, ld, lb, bm, lane, P.draw_cap)) {
                             if (lane == 0) {
                                 set_status(P.status, ST_TIMEOUT);
                                 ctl[1] = 1;

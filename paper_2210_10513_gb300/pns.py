@@ -73,7 +73,8 @@ assert STATS_DTYPE.itemsize == C.sizeof(pns_stats)
 
 EXPORTS = ("pns_create", "pns_run", "pns_run_plain", "pns_read", "pns_read_samples", "pns_moments",
            "pns_energy_grads", "pns_fields", "pns_get_info", "pns_checkpoint", "pns_restore", "pns_destroy",
-           "pns_last_error", "pns_sample_static", "pns_read_best", "pns_donuts_run", "pns_l2_read_probe")
+           "pns_last_error", "pns_sample_static", "pns_read_best", "pns_donuts_run", "pns_l2_read_probe",
+           "pns_data_energy")
 STATIC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
@@ -110,6 +111,8 @@ def lib():
         L.pns_donuts_run.restype = C.c_int
         L.pns_l2_read_probe.argtypes = [C.c_size_t, C.c_int32, C.POINTER(C.c_double), vp]
         L.pns_l2_read_probe.restype = C.c_int
+        L.pns_data_energy.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp]
+        L.pns_data_energy.restype = C.c_int
         L.pns_destroy.argtypes = [vp]
         L.pns_destroy.restype = None
         L.pns_last_error.argtypes = []
@@ -269,6 +272,12 @@ def pns_energy_grads(n, beta, scalars, mean_x, mean_xx, cov_ex, cov_exx, data_x,
     _check(lib().pns_energy_grads(int(n), C.c_float(beta), _addr(scalars), _addr(mean_x), _addr(mean_xx),
                                   _addr(cov_ex), _addr(cov_exx), _addr(data_x), _addr(data_xx),
                                   float(data_mean_energy), _addr(dQ), _addr(db), _addr(dbeta), _stream(stream)))
+
+
+def pns_data_energy(n, q, b, data_x, data_xx, out, stream=None):
+    """out[0] = sum data_xx * Q + sum data_x * b (fp64, device), pns_data_energy."""
+    _check(lib().pns_data_energy(int(n), _addr(q), _addr(b), _addr(data_x), _addr(data_xx), _addr(out),
+                                 _stream(stream)))
 
 
 def pns_fields(ctx, out, stream=None):

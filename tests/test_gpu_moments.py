@@ -143,3 +143,25 @@ def test_autograd_functions():
     ll.backward()
     assert np.abs(q.grad.cpu().numpy()).max() < 0.05
     assert abs(beta.grad.item()) < 0.05 * max(1.0, abs(m["E"]))
+
+
+def test_data_energy_kernel_equals_fp64_sum():
+    """pns_data_energy: sum_ij data_xx_ij Q_ij + sum_i data_x_i b_i in fp64
+    equals the plain fp64 sum (rounding order only), with and without b."""
+    import torch
+
+    from paper_2210_10513_gb300 import pns
+    rng = np.random.default_rng(5)
+    for n in (1, 16, 64, 300):
+        q = synth.dense_normal(n, 0.1, n)
+        b = synth.vector_normal(n, 0.1, n)
+        x = rng.uniform(0, 1, n)
+        xx = rng.uniform(0, 1, (n, n))
+        xx = (xx + xx.T) / 2
+        want = float((xx * q.astype(np.float64)).sum() + (x * b.astype(np.float64)).sum())
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+        pns.pns_data_energy(n, dev(q), dev(b), dev(x), dev(xx), out)
+        assert float(out.item()) == pytest.approx(want, rel=1e-12, abs=1e-12)
+        pns.pns_data_energy(n, dev(q), None, None, dev(xx), out)
+        assert float(out.item()) == pytest.approx(float((xx * q.astype(np.float64)).sum()), rel=1e-12, abs=1e-12)

@@ -57,14 +57,40 @@ def test_unbiased_tempering_matches_oracle(monkeypatch, integer, prefetch, block
     assert g["stats"]["swaps_accepted"].sum() > 0
 
 
-def test_metropolis_tempering_runs_and_conserves_temperatures():
-    probs = _problems([64, 64], seed=5, integer=True)
+@pytest.mark.parametrize("integer", [True, False])
+def test_metropolis_tempering_matches_oracle(integer):
+    """Metropolis (Algorithm 1) with replica exchange every swap_interval
+    records: per-slot tapes, temperatures, exchange counts, energies and
+    states equal the oracle's (two chains per temperature, uneven n)."""
+    probs = _problems([64, 96], seed=5, integer=integer)
     betas = synth.geometric_ladder(0.05, 2.0, 6)
     for p in probs:
         p["betas"] = betas
-    g = gpu_run(probs, 1000, tape=True, variant="metropolis", L0=100, swap_interval=50, chains_per_replica=2, seed=2)
-    bidx = g["stats"]["beta_idx"].reshape(4, 6)
+    cpr, swap, steps = 2, 50, 1000
+    g = gpu_run(probs, steps, tape=True, variant="metropolis", L0=100, swap_interval=swap, chains_per_replica=cpr,
+                seed=2)
+    R = len(betas)
+    for p, pr in enumerate(probs):
+        op = O.Problem(q=pr["q"])
+        for r in range(cpr):
+            grp = p * cpr + r
+            res = O.run_tempering(op, betas, dict(variant="metropolis", L0=100, seed=2), group_id=grp,
+                                  chain_id0=grp * R, x0s=[np.zeros(pr["n"], np.uint8)] * R, rounds=steps // swap,
+                                  periods_per_round=swap)
+            for s in range(R):
+                cid = grp * R + s
+                o = res[s]
+                rec = int(g["stats"]["tape_records"][cid])
+                assert rec == len(o["flips"]) == steps
+                np.testing.assert_array_equal(g["flips"][cid, :rec], o["flips"])
+                assert (g["m"][cid, :rec] == 1.0).all()
+                st = g["stats"][cid]
+                assert st["beta_idx"] == o["state"].beta_idx
+                assert st["swaps_accepted"] == o["state"].swaps_accepted
+                assert st["energy"] == o["state"].E
+                bits = synth.unpack_bits(g["states"][cid:cid + 1], pr["n"])[0]
+                np.testing.assert_array_equal(bits, o["x"])
+    bidx = g["stats"]["beta_idx"].reshape(-1, R)
     for row in bidx:
-        assert sorted(row.tolist()) == list(range(6))
-    assert (g["stats"]["steps"] == 1000).all()
+        assert sorted(row.tolist()) == list(range(R))
     assert g["stats"]["swaps_accepted"].sum() > 0

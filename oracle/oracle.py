@@ -30,7 +30,8 @@ class _Problem(C.Structure):
 
 class _Config(C.Structure):
     _fields_ = [("variant", C.c_int32), ("k", C.c_int32), ("subset", C.c_int32), ("pad", C.c_int32),
-                ("L0", C.c_int64), ("seed", C.c_uint64)]
+                ("L0", C.c_int64), ("seed", C.c_uint64), ("anneal_start", C.c_float), ("pad2", C.c_int32),
+                ("anneal_steps", C.c_int64)]
 
 
 class _Chain(C.Structure):
@@ -156,13 +157,18 @@ class ChainState:
         self.x_best = self.x.copy()  # X_max of Algorithms 8-10
 
 
-def make_config(variant, k=0, subset="systematic", L0=100, seed=0):
+def make_config(variant, k=0, subset="systematic", L0=100, seed=0, anneal_start=1.0, anneal_steps=0):
+    """anneal_start s0 and anneal_steps K: the cooling schedule of
+    Algorithms 8-10, record k at inverse temperature beta s0^(1 - k/K) for
+    k < K (K = 0: constant temperature)."""
     c = _Config()
     c.variant = VARIANTS[variant]
     c.k = int(k)
     c.subset = SUBSETS[subset]
     c.L0 = int(L0)
     c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    c.anneal_start = float(anneal_start)
+    c.anneal_steps = int(anneal_steps)
     return c
 
 

@@ -218,7 +218,25 @@ typedef struct {
     int32_t pad;
     int64_t L0;
     uint64_t seed;
+    /* Cooling schedule T(k) of Algorithms 8-10 (Sec. 8.1), non-increasing:
+     * record k (k = 1, 2, ...) targets pi^{1/T(k)}, i.e. inverse temperature
+     * beta / T(k) = beta s_k with s_k = s0^(1 - k/K) for k < K and 1 from
+     * k = K on (geometric cooling from T = 1/s0 down to T = 1).
+     * anneal_steps = K = 0: T = 1 throughout. */
+    float anneal_start;      /* s0, in (0, 1] */
+    int32_t pad2;
+    int64_t anneal_steps;    /* K */
 } oq_config;
+
+/* beta / T(k) for record k of the schedule, in fp32:
+ * r = k / K, y = ln(s0) (1 - r), beta exp(y). */
+static float anneal_beta(const oq_config *C, float beta, float ln_s0, int64_t k)
+{
+    if (C->anneal_steps <= 0 || k >= C->anneal_steps) return beta;
+    float r = (float)k / (float)C->anneal_steps;
+    float y = ln_s0 * (1.0f - r);
+    return beta * oq_expf(y);
+}
 
 /* Per-chain state (one per chain, owned by the caller). */
 typedef struct {
@@ -481,11 +499,15 @@ int oq_run_chain(const oq_problem *P, const oq_config *C, float beta, uint32_t c
     if (!cand || !d_i || !d_f) { free(cand); free(d_i); free(d_f); return 2; }
     int rc = 0;
     int64_t rec = 0, periods = 0;
+    const float ln_s0 = C->anneal_steps > 0 ? oq_logf(C->anneal_start) : 0.0f;
+    const float beta_chain = beta;
     while (rec < max_records) {
         if (stop_after_periods > 0 && periods >= stop_after_periods) break;
         uint64_t step = (uint64_t)S->step;
         int32_t flip = -1;
         double m = 1.0;
+        /* the record's inverse temperature: record k = step + 1 of the chain */
+        beta = anneal_beta(C, beta_chain, ln_s0, (int64_t)step + 1);
         if (C->variant == V_METROPOLIS) {
             /* Algorithm 1: propose a uniform neighbour, accept w.p. min(1, e^{-beta Delta}). */
             uint32_t w2 = rng_word(C->seed, TAG_STEP, chain, step, 2);

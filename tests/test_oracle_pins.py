@@ -547,3 +547,68 @@ def test_one_unbiased_record_against_its_law():
             assert 1 <= ms[0] <= L0
     chi2 = (((counts - draws * want) ** 2) / (draws * want)).sum()
     assert chi2 < 25.0, (counts, draws * want)
+
+
+# ---------------------------------------------------------------------------
+# Cooling schedule of the optimisation forms (Algorithms 8-10, Sec. 8.1).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 9])
+def test_anneal_schedule_one_step_law(k):
+    """Record k of Simulated Annealing (Algorithm 8) accepts an uphill move
+    of size d with probability [pi(y)/pi(x)]^{1/T(k)} = e^{-beta d / T(k)},
+    1/T(k) = s0^(1 - k/K) for k < K and 1 from K on.  One bit, d = 3, beta =
+    0.5, s0 = 0.25, K = 4: the first record of 40,000 chains started at step
+    k - 1 against the closed form."""
+    d, beta, s0, K = 3, 0.5, 0.25, 4
+    p = O.Problem(q=np.array([[d]], dtype=np.int32))
+    c = O.make_config("metropolis", L0=100, seed=17, anneal_start=s0, anneal_steps=K)
+    N = 40000
+    acc = 0
+    for chain in range(N):
+        st = O.ChainState(p, np.zeros(1, np.uint8), 100)
+        st.st.step = k - 1
+        fl, _ = O.run_chain(p, c, beta, chain, st, 1)
+        acc += int(fl[0] == 0)
+    inv_t = s0 ** (1.0 - k / K) if k < K else 1.0
+    want = math.exp(-beta * d * inv_t)
+    assert abs(acc / N - want) < 5 * math.sqrt(want * (1 - want) / N), (k, acc / N, want)
+
+
+def test_anneal_start_one_is_constant_temperature():
+    """s0 = 1 gives T(k) = 1 for every k: the tapes equal the runs without a
+    schedule (Sec. 8.2's setting), for every variant."""
+    Q = synth.dense_int(20, -15, 15, seed=6, dtype=np.int32)
+    p = O.Problem(q=Q)
+    for variant in ("metropolis", "rf", "basic", "unbiased"):
+        a = O.make_config(variant, k=5, L0=50, seed=2)
+        b = O.make_config(variant, k=5, L0=50, seed=2, anneal_start=1.0, anneal_steps=300)
+        sa = O.ChainState(p, np.zeros(20, np.uint8), 50)
+        sb = O.ChainState(p, np.zeros(20, np.uint8), 50)
+        fa, ma = O.run_chain(p, a, 0.4, 3, sa, 500)
+        fb, mb = O.run_chain(p, b, 0.4, 3, sb, 500)
+        np.testing.assert_array_equal(fa, fb)
+        np.testing.assert_array_equal(ma, mb)
+
+
+def test_annealing_reaches_the_ground_state():
+    """Simulated Annealing, Optimization RF and Optimization PNS with a slow
+    geometric cooling end with X_max at the exact minimum of E (enumerated
+    over all 2^14 states) on most chains, and X_max is the lowest state the
+    replayed path visits."""
+    n = 14
+    Q = synth.dense_int(n, -10, 10, seed=21, dtype=np.int32)
+    p = O.Problem(q=Q)
+    E = X.energies(Q, None)
+    emin = E.min()
+    for variant, k, recs in (("metropolis", 1, 6000), ("rf", 0, 600), ("basic", 4, 1500)):
+        c = O.make_config(variant, k=k, L0=100, seed=8, anneal_start=0.02, anneal_steps=recs)
+        hits = 0
+        for chain in range(16):
+            st = O.ChainState(p, np.zeros(n, np.uint8), 100)
+            fl, _ = O.run_chain(p, c, 0.5, chain, st, recs)
+            codes, last = X.replay_codes(0, fl)
+            visited = np.append(codes, last)
+            assert st.st.best_E == E[visited].min() == E[X.code_of(st.x_best)]
+            hits += int(st.st.best_E == emin)
+        assert hits >= 12, (variant, hits)

@@ -121,9 +121,18 @@ typedef struct {
     int32_t track_best;        /* 1: keep each chain's lowest-energy state X_max, the output of the
                                   optimisation forms (Algorithms 8-10: with variant BASIC this is
                                   Optimization PNS, with RF Optimization Rejection-Free, at the
-                                  constant temperature 1/beta); read it with pns_read_best.  Runs
-                                  on the per-flip kernel. */
+                                  constant temperature 1/beta, or on the cooling schedule below);
+                                  read it with pns_read_best.  Runs on the per-flip kernel. */
     int32_t reserved;          /* must be 0 */
+    float anneal_start;        /* cooling schedule T(k) of Algorithms 8-10 (Sec. 8.1): s0 in (0, 1];
+                                  with anneal_steps = K > 0, record k = 1, 2, ... of a chain (k counts
+                                  the chain's records from its start) targets pi^{1/T(k)}, i.e. runs at
+                                  inverse temperature beta s_k, s_k = s0^(1 - k/K) for k < K and 1 from
+                                  k = K on (geometric cooling from T = 1/s0 to T = 1), in fp32:
+                                  beta * det_exp(det_log(s0) * (1 - k/K)).  No replica exchange; runs
+                                  on the per-flip kernel.  Ignored when anneal_steps = 0. */
+    int32_t reserved2;         /* must be 0 */
+    int64_t anneal_steps;      /* K >= 0; 0: constant temperature */
 } pns_config;
 
 /* Chain numbering: instance p, chain r of each temperature, replica slot s:

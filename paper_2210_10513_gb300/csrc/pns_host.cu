@@ -173,6 +173,14 @@ pns_status check_args(const pns_problem *probs, int32_t n_probs, const pns_confi
     if (cfg->track_best != 0 && cfg->track_best != 1) return fail(PNS_ERR_INVALID_ARG, "track_best must be 0 or 1");
     if (cfg->chains_per_cta < 0 || cfg->reserved != 0 || cfg->chain_base < 0 || cfg->group_base < 0)
         return fail(PNS_ERR_INVALID_ARG, "chains_per_cta, chain_base, group_base must be >= 0 and reserved 0");
+    if (cfg->reserved2 != 0 || cfg->anneal_steps < 0)
+        return fail(PNS_ERR_INVALID_ARG, "anneal_steps must be >= 0 and reserved2 0");
+    if (cfg->anneal_steps > 0) {
+        if (!(cfg->anneal_start > 0.0f) || !(cfg->anneal_start <= 1.0f))
+            return fail(PNS_ERR_INVALID_ARG, "anneal_start must be in (0, 1]");
+        if (cfg->swap_interval > 0)
+            return fail(PNS_ERR_UNSUPPORTED, "a cooling schedule with replica exchange is not supported");
+    }
     if (cfg->swap_interval > 0) {
         if (cfg->variant != PNS_UNBIASED && cfg->variant != PNS_METROPOLIS)
             return fail(PNS_ERR_INVALID_ARG, "replica exchange needs PNS_UNBIASED or PNS_METROPOLIS");
@@ -618,7 +626,7 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
         m.spec = (d == 0 || spec_supported(c.qtype, d)) ? d : 0;
     }
     if (m.spec > 0 && !spec_allowed(c)) m.spec = 0;
-    if (cfg->track_best) m.spec = 0;  // X_max is kept by the per-flip kernel
+    if (cfg->track_best || cfg->anneal_steps > 0) m.spec = 0;  // X_max and the schedule: the per-flip kernel
     if (m.spec > 0) m.prod = 0;
     // The set sweep (systematic sets) evaluates each set once per state
     // instead of once per record.
@@ -632,6 +640,7 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
     // every exchange group (whose hottest replica sets the pace).
     m.block = block_allowed(c) && cfg->warps_per_chain <= 1 && !cfg->track_best ? 1 : 0;
     if (const char *e = getenv("PNS_BLOCKED")) m.block = atoi(e) && block_allowed(c) && !cfg->track_best ? 1 : 0;
+    if (cfg->anneal_steps > 0) m.sweep = 0;
     if (m.block) {
         m.T = 1;
         m.prod = 0;
@@ -763,7 +772,7 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         if (m.spec > 0 && (!spec_allowed(*c) || !spec_supported(c->qtype, m.spec))) return;
         if (m.sweep && (m.spec <= 0 || !sweep_allowed(*c, m.spec))) return;
         if (m.block && (!block_allowed(*c) || m.T != 1)) return;
-        if (c->cfg.track_best && (m.block || m.spec > 0)) return;
+        if ((c->cfg.track_best || c->cfg.anneal_steps > 0) && (m.block || m.spec > 0)) return;
         for (const Mapping &o : cands)
             if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta && o.block == m.block &&
                 o.gw == m.gw && o.sweep == m.sweep)
@@ -1270,6 +1279,8 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     // a host-set cap on the draws of a random k-subset (tests make the bounded
     // loop give up with it); read at each run, baked into a graph when captured
     if (const char *e = getenv("PNS_DRAW_CAP")) P.draw_cap = static_cast<uint32_t>(strtoul(e, nullptr, 10));
+    P.anneal_start = c->cfg.anneal_start;
+    P.anneal_steps = c->cfg.anneal_steps;
     if (fault_injected("launch")) return fail(PNS_ERR_CUDA, "injected launch failure (PNS_FAULT)");
     P.chain_base = static_cast<uint32_t>(c->cfg.chain_base);
     P.group_base = static_cast<uint32_t>(c->cfg.group_base);

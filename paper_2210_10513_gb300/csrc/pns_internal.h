@@ -92,7 +92,8 @@ struct KParams {
     const float4 *wtab;     // integer Q: weight tables e^{-beta d}, d = 0, 1, ... (w, its two quantised parts)
     const int2 *wtab_desc;  // per chain: (first entry, entries); entries 0 = no table
     uint32_t draw_cap;      // 0, or the most draws a random k-subset may take (host-set, for tests)
-    uint32_t pad2;
+    float anneal_start;     // cooling schedule (Algorithms 8-10): s0, used when anneal_steps > 0
+    int64_t anneal_steps;   // K: record k < K runs at beta s0^(1 - k/K); 0 = constant temperature
 };
 
 PNS_HD int32_t round16(int32_t b) { return (b + 15) & ~15; }

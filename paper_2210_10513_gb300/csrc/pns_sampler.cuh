@@ -229,6 +229,15 @@ __device__ __forceinline__ Mult multiplicity_e1(uint64_t S, int32_t k, float anc
     return mult_from(p, c, e1);
 }
 
+// beta / T(k) for record k of the cooling schedule of Algorithms 8-10: beta
+// s0^(1 - k/K) for k < K, in fp32 as det_exp(ln(s0) (1 - k/K)) with IEEE
+// division and products; beta itself when K = 0 or k >= K.
+__device__ __forceinline__ float anneal_beta(float beta, float ln_s0, int64_t K, int64_t k) {
+    if (K <= 0 || k >= K) return beta;
+    const float r = __fdiv_rn(__ll2float_rn(k), __ll2float_rn(K));
+    return __fmul_rn(beta, det_expf(__fmul_rn(ln_s0, __fsub_rn(1.0f, r))));
+}
+
 // First k distinct values of v_m = floor(word_m n / 2^32), m = 0, 1, ...,
 // drawn by one warp into `list`.  Returns false when the draw cap is hit:
 // 64 n + 1024 draws, or `cap_limit` when that is smaller and nonzero (a
@@ -400,7 +409,8 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
 
     // ---- consumers ------------------------------------------------------------
     const int ctid = tid;
-    float beta = in.betas[st.beta_idx];
+    float beta_chain = in.betas[st.beta_idx];
+    const float anneal_ls0 = P.anneal_steps > 0 ? det_logf(P.anneal_start) : 0.0f;
     int dead = 0;
     bool list_valid = false;
     int64_t tape_pos = 0;
@@ -545,6 +555,9 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
     auto one_record = [&]() -> bool {
         sample_record();
         const uint64_t step = static_cast<uint64_t>(st.step);
+        // the record's inverse temperature: beta / T(k) of the cooling schedule
+        // (Algorithms 8-10) for record k = step + 1, else the chain's beta
+        const float beta = anneal_beta(beta_chain, anneal_ls0, P.anneal_steps, static_cast<int64_t>(step) + 1);
         const unsigned char *slot = base + L.slots + cur * L.slot_bytes;
         RecordDraws rd;
         if (prod > 0) {
@@ -894,7 +907,7 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
                     st.swaps += *swap_cnt;
                     sync_cons();
                     if (ctid == 0) *swap_cnt = 0;
-                    beta = in.betas[st.beta_idx];
+                    beta_chain = in.betas[st.beta_idx];
                 }
                 end_record(!(done == per_round && rdi + 1 == rounds));
             }

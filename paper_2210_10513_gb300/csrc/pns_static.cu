@@ -168,6 +168,10 @@ pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int
     if (cfg->chains_per_cta < 0 || cfg->reserved != 0 || cfg->chain_base < 0 || cfg->group_base < 0)
         return sfail(PNS_ERR_INVALID_ARG, "chains_per_cta, chain_base, group_base must be >= 0 and reserved 0");
     if (prob->k < 0 || prob->reserved != 0) return sfail(PNS_ERR_INVALID_ARG, "problem: k < 0 or reserved != 0");
+    if (cfg->reserved2 != 0 || cfg->anneal_steps < 0)
+        return sfail(PNS_ERR_INVALID_ARG, "anneal_steps must be >= 0 and reserved2 0");
+    if (cfg->anneal_steps > 0 && (!(cfg->anneal_start > 0.0f) || !(cfg->anneal_start <= 1.0f)))
+        return sfail(PNS_ERR_INVALID_ARG, "anneal_start must be in (0, 1]");
     // what this entry point does not do
     if (cfg->track_best) return sfail(PNS_ERR_UNSUPPORTED, "pns_sample_static keeps no best states (track_best)");
     if (cfg->tape == 2) return sfail(PNS_ERR_UNSUPPORTED, "pns_sample_static writes no sample tape (tape = 2)");
@@ -327,6 +331,8 @@ pns_status pns_sample_static(const pns_problem *prob, const pns_config *cfg, int
     P.tape = (flips && multiplicities) ? 1 : 0;
     P.prod = 0;
     P.chain_base = static_cast<uint32_t>(cfg->chain_base);
+    P.anneal_start = cfg->anneal_start;
+    P.anneal_steps = cfg->anneal_steps;
     if (steps > 0)
         SCU(launch_sampler(PNS_DENSE, qt, 4, T, P, static_cast<int>(ctas), per_cta * 32 * T,
                            static_cast<size_t>(per_cta) * chain_bytes, s));

@@ -42,7 +42,8 @@ class pns_config(C.Structure):
                 ("L0", C.c_int64), ("swap_interval", C.c_int64), ("seed", C.c_uint64), ("tape", C.c_int32),
                 ("warps_per_chain", C.c_int32), ("chains_per_cta", C.c_int32), ("chain_base", C.c_int32),
                 ("x0", C.c_void_p), ("group_base", C.c_int32), ("graph", C.c_int32), ("autotune", C.c_int32),
-                ("track_best", C.c_int32), ("reserved", C.c_int32)]
+                ("track_best", C.c_int32), ("reserved", C.c_int32), ("anneal_start", C.c_float),
+                ("reserved2", C.c_int32), ("anneal_steps", C.c_int64)]
 
 
 class pns_info(C.Structure):
@@ -207,7 +208,7 @@ def make_problem(n, q=None, b=None, betas=(1.0,), csr=None, k=0, keep=None):
 
 def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100, swap_interval=0, seed=0,
                 tape=False, warps_per_chain=0, x0=None, chains_per_cta=0, chain_base=0, group_base=0, graph=False,
-                autotune=False, track_best=False):
+                autotune=False, track_best=False, anneal_start=1.0, anneal_steps=0):
     c = pns_config()
     c.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     c.k = int(k)
@@ -224,6 +225,8 @@ def make_config(variant="unbiased", k=1, subset="systematic", chains_per_replica
     c.graph = int(bool(graph))
     c.autotune = int(bool(autotune))
     c.track_best = int(bool(track_best))
+    c.anneal_start = float(anneal_start)
+    c.anneal_steps = int(anneal_steps)
     c.x0 = _addr(x0)
     return c
 
@@ -323,7 +326,8 @@ class Sampler:
 
     def __init__(self, problems, variant="unbiased", k=1, subset="systematic", chains_per_replica=1, L0=100,
                  swap_interval=0, seed=0, tape=False, warps_per_chain=0, x0=None, stream=None, chains_per_cta=0,
-                 chain_base=0, group_base=0, graph=False, autotune=False, track_best=False):
+                 chain_base=0, group_base=0, graph=False, autotune=False, track_best=False, anneal_start=1.0,
+                 anneal_steps=0):
         keep = []
         probs = []
         for pr in problems:
@@ -331,7 +335,8 @@ class Sampler:
         if x0 is not None:
             keep.append(x0)
         cfg = make_config(variant, k, subset, chains_per_replica, L0, swap_interval, seed, tape, warps_per_chain, x0,
-                          chains_per_cta, chain_base, group_base, graph, autotune, track_best)
+                          chains_per_cta, chain_base, group_base, graph, autotune, track_best, anneal_start,
+                          anneal_steps)
         self.ctx = pns_create(probs, cfg, stream)
         self.info = pns_get_info(self.ctx)
         self.tape = bool(tape)

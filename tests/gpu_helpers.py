@@ -54,7 +54,8 @@ def oracle_problem(p):
 
 def oracle_run(problems, steps, chain_ids, x0=None, **cfg):
     okw = dict(variant=cfg.get("variant", "unbiased"), k=cfg.get("k", 1), subset=cfg.get("subset", "systematic"),
-               L0=cfg.get("L0", 100), seed=cfg.get("seed", 0))
+               L0=cfg.get("L0", 100), seed=cfg.get("seed", 0), anneal_start=cfg.get("anneal_start", 1.0),
+               anneal_steps=cfg.get("anneal_steps", 0))
     oprobs = [oracle_problem(p) for p in problems]
     betas = [list(np.asarray(p["betas"], dtype=np.float32)) for p in problems]
     x0d = None

@@ -53,6 +53,51 @@ def test_best_states_match_oracle(variant, k):
         np.testing.assert_array_equal(g["m"][cid], plain["m"][cid])
 
 
+@pytest.mark.parametrize("variant,k,subset", [("metropolis", 1, "systematic"), ("rf", 0, "systematic"),
+                                              ("basic", 8, "systematic"), ("unbiased", 8, "random")])
+def test_cooling_schedule_matches_oracle(variant, k, subset):
+    """Algorithms 8-10 with the cooling schedule T(k) (geometric from
+    T = 1/0.05 to 1 over the first 1000 records, then constant): Simulated
+    Annealing (Metropolis), Optimization RF and Optimization PNS (Basic), and
+    Unbiased PNS on the same schedule.  Tapes, X_max, best energies and
+    states equal the oracle's; a run split in two launches gives the same
+    records (the schedule counts the chain's records, not the launch's)."""
+    p = _prob(64, seed=4)
+    chains = 5
+    cfg = dict(variant=variant, k=k, subset=subset, chains_per_replica=chains, seed=7, L0=50, anneal_start=0.05,
+               anneal_steps=1000)
+    g = _best_gpu([p], 1500, **cfg)
+    ref = oracle_run([p], 1500, list(range(chains)), **cfg)
+    for cid in range(chains):
+        r = ref[cid]
+        np.testing.assert_array_equal(g["flips"][cid], r["flips"])
+        np.testing.assert_array_equal(g["m"][cid], r["m"])
+        bits = synth.unpack_bits(g["best"][cid:cid + 1], 64)[0]
+        np.testing.assert_array_equal(bits, r["x_best"])
+        assert g["stats"][cid]["best_energy"] == r["state"].best_E
+        assert g["stats"][cid]["energy"] == r["state"].E
+    from paper_2210_10513_gb300 import pns
+    d = dict(p)
+    d["q"], d["b"] = to_dev(d["q"]), to_dev(d["b"])
+    s = pns.Sampler([d], tape=False, **cfg)
+    s.run(700)
+    s.run(800)
+    st = s.read(tape=False)["stats"]
+    s.close()
+    np.testing.assert_array_equal(st["energy"], g["stats"]["energy"])
+    np.testing.assert_array_equal(st["flips"], g["stats"]["flips"])
+
+
+def test_cooling_schedule_argument_checks():
+    from paper_2210_10513_gb300 import pns
+    p = _prob(32, seed=1)
+    for kw, status in ((dict(anneal_start=0.0, anneal_steps=10), 1), (dict(anneal_start=1.5, anneal_steps=10), 1),
+                       (dict(anneal_steps=-1), 1), (dict(anneal_start=0.5, anneal_steps=10, swap_interval=100), 8)):
+        with pytest.raises(pns.PnsError) as ei:
+            pns.Sampler([dict(p)], variant="unbiased", k=4, **kw)
+        assert ei.value.status == status, kw
+
+
 def test_best_state_survives_checkpoint():
     from paper_2210_10513_gb300 import pns
     p = _prob(40, seed=8)

@@ -575,6 +575,298 @@ __device__ __forceinline__ bool block_period(const KParams &P, const BlockChain<
     return period_end;
 }
 
+// The narrow record forms (PPL 1 or 2: at most 62 positions, lane 31 free)
+// with the record loop software-pipelined.  A record's race fixes its winner
+// before its multiplicity is known; the chain applies the winner's move to a
+// copy of its set state at once and evaluates the next record on that copy
+// while the current record's multiplicity and budget test run (the two
+// dependent chains interleave in one basic block).  If the test says move,
+// the copy becomes the state and the next record is already evaluated; if it
+// says stay, the period ends and the evaluation is dropped.  The records, and
+// every value they produce, are those of block_period.
+template <typename QT, typename HT, int PPL>
+__device__ __forceinline__ bool block_period_pipe(const KParams &P, const BlockChain<QT, HT> &c) {
+    static_assert(PPL == 1 || PPL == 2, "narrow forms");
+    using A = Arith<HT>;
+    using D = typename A::D;
+    using CT = typename A::C;
+    const int cid = c.cid, n = c.n, k = c.k, kp = c.kp, s0 = c.s0, lane = c.lane, ld = c.ld;
+    const uint32_t chain_id = c.chain_id;
+    const uint64_t seed = P.seed;
+    const int tape = P.tape;
+    const int64_t tape_cap = P.tape_cap;
+    const int32_t L0 = static_cast<int32_t>(P.L0);
+    const uint32_t row_bytes = c.row_bytes;
+    const QT *const Q = c.Q;
+    const QT *const sub = c.sub;
+    HT *const insf = c.insf;
+    uint32_t *const xw = c.xw;
+    int32_t *const log = c.log;
+    ChainState *const cs = c.cs;
+    int64_t stp = cs->step;
+    int32_t Lb = static_cast<int32_t>(cs->L);
+    double E = cs->E, bestE = cs->best_E;
+    int32_t nflip = 0, nsat = 0;
+    const int64_t step0 = c.step0;
+    const float beta = c.beta;
+    const int t0 = PPL * lane;
+    const int tb = t0 < kp - PPL ? t0 : kp - PPL;
+    HT hv[PPL];
+    ld_vec<PPL>(insf + tb, hv);
+    const CT *const sbp = c.sub_b + tb;
+    const CT *const sdp = c.sub_d + tb;
+    uint32_t xb = 0u;
+#pragma unroll
+    for (int u = 0; u < PPL; ++u) {
+        int i = s0 + (t0 + u < k ? t0 + u : 0);
+        i = i >= n ? i - n : i;
+        xb |= ((xw[i >> 5] >> (i & 31)) & 1u) << u;
+    }
+    const int per = (kp >> 2) + 1;
+    const int B = 64 / per < 2 ? 2 : (64 / per > DRAW_MAXB ? DRAW_MAXB : 64 / per);
+    float *const xbuf = c.wbuf;
+    float *const e1buf = c.wbuf + DRAW_BUF;
+    int bi = B;
+    const bool anchor_lane = lane == 31;  // (k <= 31 PPL: lane 31 holds no position)
+    int len = 0, nrec = 0;
+    int32_t pend_flip = 0, pend_m = 0;
+    int64_t pend_pos = -1;
+    int64_t sum_i = 0;
+    auto flush_record = [&]() {
+        if (pend_pos >= 0) {
+            if (lane == 0 && tape >= 1 && pend_pos < tape_cap) {
+                const int64_t o = static_cast<int64_t>(cid) * tape_cap + pend_pos;
+                P.tape_flip[o] = pend_flip;
+                P.tape_m[o] = static_cast<double>(pend_m);
+            }
+            sum_i += pend_m;
+            bestE = fmin(bestE, E);
+        }
+        pend_pos = -1;
+    };
+    auto write_record = [&](int32_t flip, int32_t m) {
+        pend_flip = flip;
+        pend_m = m;
+        pend_pos = stp - step0;
+    };
+    // the draws of record step (batch index bi), refilled outside the
+    // pipelined region
+    auto ensure_draws = [&](uint64_t step) {
+        if (bi == B) {
+            __syncwarp();
+            batch_draws(seed, chain_id, step, B, kp, per, lane, xbuf, e1buf);
+            __syncwarp();
+            bi = 0;
+        }
+    };
+    // evaluation of one record on the set state (h, x): the race winner, its
+    // delta and bit, the quantised weight sum and the anchor's weight
+    struct Eval {
+        uint32_t SA, SB;
+        int a;
+        D dj;
+        bool xj;
+        float af, anchor_e, e1;
+    };
+    auto evaluate = [&](const HT (&h)[PPL], uint32_t xbits, int bidx) -> Eval {
+        float ex[PPL];
+        ld_vec<PPL>(xbuf + bidx * kp + tb, ex);
+        CT bv[PPL], dv[PPL];
+        ld_vec<PPL>(sbp, bv);
+        ld_vec<PPL>(sdp, dv);
+        D dl[PPL];
+        uint32_t lmin = 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+            dl[u] = A::delta(h[u], bv[u], dv[u], (xbits >> u) & 1u);
+            const uint32_t kd = A::key(A::pos(dl[u]));
+            lmin = t0 + u < k && kd < lmin ? kd : lmin;
+        }
+        Eval r;
+        r.e1 = e1buf[bidx];
+        const D amin = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin));
+        r.af = A::tof(amin);
+        uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
+        D dbest = dl[0];
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+            const int t = t0 + u;
+            const bool ins = t < k;
+            const float dv_u = (u == 0 && anchor_lane) ? r.af : A::diff(A::pos(dl[u]), amin);
+            const float w = det_expf(-__fmul_rn(beta, dv_u));
+            if (u == 0) r.anchor_e = __shfl_sync(0xFFFFFFFFu, w, 31);
+            const float ws = __fmul_rn(w, 65536.0f);
+            const float wa = truncf(ws);
+            const uint32_t qa = __float2uint_rz(wa);
+            const uint32_t qb = __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
+            sa += ins ? qa : 0u;
+            sb += ins ? qb : 0u;
+            const uint32_t kb = ins ? __float_as_uint(race_key(ex[u], w)) : 0xFFFFFFFFu;
+            const bool better = kb < bkey;
+            bkey = better ? kb : bkey;
+            bpos = better ? static_cast<uint32_t>(t) : bpos;
+            dbest = better ? dl[u] : dbest;
+        }
+        const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
+        const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
+        r.SA = __reduce_add_sync(0xFFFFFFFFu, sa);
+        r.SB = __reduce_add_sync(0xFFFFFFFFu, sb);
+        r.a = static_cast<int>(wpos);
+        const int owner = r.a / PPL;
+        r.dj = shfl_d(dbest, owner);
+        r.xj = __ballot_sync(0xFFFFFFFFu, lane == owner && ((xbits >> (r.a - t0)) & 1u)) != 0u;
+        return r;
+    };
+    auto tape2 = [&]() {
+        if (tape == 2) {
+            const int64_t pos = stp - step0;
+            if (pos < tape_cap) {
+                const int64_t o = static_cast<int64_t>(cid) * tape_cap + pos;
+                uint32_t *tx = P.tape_x + o * P.W;
+                for (int q = lane; q < P.W; q += 32) tx[q] = q < ld / 32 ? xw[q] : 0u;
+                if (lane == 0) P.tape_E[o] = E;
+            }
+        }
+    };
+
+    tape2();
+    ensure_draws(static_cast<uint64_t>(stp));
+    Eval ev = evaluate(hv, xb, bi);
+    bi += 1;
+    bool period_end = false;
+    while (true) {
+        // record stp is evaluated (ev); its successor's draws come next
+        ensure_draws(static_cast<uint64_t>(stp) + 1);
+        const int a = ev.a;
+        const int owner = a / PPL;
+        int j = s0 + a;
+        j = j >= n ? j - n : j;
+        const bool up = !ev.xj;
+        // the move of record stp, tentatively
+        QT qv[PPL];
+        ld_vec<PPL>(sub + a * kp + tb, qv);
+        HT hn[PPL];
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) hn[u] = add_elem<QT, HT>(hv[u], qv[u], up);
+        const uint32_t xn = xb ^ (lane == owner ? 1u << (a - t0) : 0u);
+        // record stp's multiplicity and budget test (branch-free) beside the
+        // evaluation of record stp + 1 on the moved state, written in stages
+        // between the warp collectives so that the two chains interleave
+        //   M1: the weight sum in fp32           E1: deltas of the moved state
+        float ex[PPL];
+        ld_vec<PPL>(xbuf + bi * kp + tb, ex);
+        CT bv[PPL], dv[PPL];
+        ld_vec<PPL>(sbp, bv);
+        ld_vec<PPL>(sdp, dv);
+        const float anchor_f = ev.af > 0.0f ? ev.anchor_e : 1.0f;
+        const float sf = __fadd_rn(__fmul_rn(__uint2float_rn(ev.SA), 65536.0f), __uint2float_rn(ev.SB));
+        D dl[PPL];
+        uint32_t lmin = 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+            dl[u] = A::delta(hn[u], bv[u], dv[u], (xn >> u) & 1u);
+            const uint32_t kd = A::key(A::pos(dl[u]));
+            lmin = t0 + u < k && kd < lmin ? kd : lmin;
+        }
+        Eval nx;
+        nx.e1 = e1buf[bi];
+        //   M2: p                                  E2: the anchor
+        const float p = __fmul_rn(div_rn_pos(__fmul_rn(sf, 0x1p-32f), __int2float_rn(k)), anchor_f);
+        const D amin = A::unkey(__reduce_min_sync(0xFFFFFFFFu, lmin));
+        nx.af = A::tof(amin);
+        //   M3: -ln(1 - p)                         E3: weights, keys, parts of the sum
+        const float cser = neg_log1m_series(p);
+        const float clog = -det_logf(__fsub_rn(1.0f, p));
+        uint32_t bkey = 0xFFFFFFFFu, bpos = 0xFFFFFFFFu, sa = 0u, sb = 0u;
+        D dbest = dl[0];
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+            const int t = t0 + u;
+            const bool ins = t < k;
+            const float dv_u = (u == 0 && anchor_lane) ? nx.af : A::diff(A::pos(dl[u]), amin);
+            const float w = det_expf(-__fmul_rn(beta, dv_u));
+            if (u == 0) nx.anchor_e = __shfl_sync(0xFFFFFFFFu, w, 31);
+            const float ws = __fmul_rn(w, 65536.0f);
+            const float wa = truncf(ws);
+            const uint32_t qa = __float2uint_rz(wa);
+            const uint32_t qb = __float2uint_rz(__fmul_rn(__fsub_rn(ws, wa), 65536.0f));
+            sa += ins ? qa : 0u;
+            sb += ins ? qb : 0u;
+            const uint32_t kb = ins ? __float_as_uint(race_key(ex[u], w)) : 0xFFFFFFFFu;
+            const bool better = kb < bkey;
+            bkey = better ? kb : bkey;
+            bpos = better ? static_cast<uint32_t>(t) : bpos;
+            dbest = better ? dl[u] : dbest;
+        }
+        //   M4: the multiplicity                   E4: the race winner and the sum
+        const Mult mu = mult_from(p, p < 0.0625f ? cser : clog, ev.e1);
+        const uint32_t wkey = __reduce_min_sync(0xFFFFFFFFu, bkey);
+        const uint32_t wpos = __reduce_min_sync(0xFFFFFFFFu, bkey == wkey ? bpos : 0xFFFFFFFFu);
+        nx.SA = __reduce_add_sync(0xFFFFFFFFu, sa);
+        nx.SB = __reduce_add_sync(0xFFFFFFFFu, sb);
+        nx.a = static_cast<int>(wpos);
+        const int nowner = nx.a / PPL;
+        nx.dj = shfl_d(dbest, nowner);
+        nx.xj = __ballot_sync(0xFFFFFFFFu, lane == nowner && ((xn >> (nx.a - t0)) & 1u)) != 0u;
+        const bool fits = mult_fits_small(mu, Lb);
+        flush_record();
+        if (fits) {
+            const int32_t m = mu.mi >= 0 ? static_cast<int32_t>(mu.mi) : __float2int_rz(mu.fgl) + 1;
+            Lb -= m;
+            nsat += mu.sat ? 1 : 0;
+            prefetch_l2_lane0(Q + static_cast<int64_t>(j) * ld, row_bytes, lane);
+            const uint32_t xword = xw[j >> 5] ^ (1u << (j & 31));
+            xw[j >> 5] = xword;
+            log[len] = j | (up ? static_cast<int32_t>(0x80000000u) : 0);
+            len += 1;
+            E = __dadd_rn(E, A::tod(ev.dj));
+            nflip += 1;
+            write_record(j, m);
+#pragma unroll
+            for (int u = 0; u < PPL; ++u) hv[u] = hn[u];
+            xb = xn;
+            ev = nx;
+            bi += 1;
+        } else {
+            const int32_t m = Lb;
+            Lb = L0;
+            if (lane == 0) {
+                int ns = cs->set_start + k;
+                while (ns >= n) ns -= n;
+                cs->stays += 1;
+                cs->set_start = ns;
+                cs->period_start = static_cast<int64_t>(stp) + 1;
+            }
+            period_end = true;
+            write_record(-1, m);
+        }
+        stp += 1;
+        nrec += 1;
+        if (period_end || len == BLOCK_LOG) break;
+        if (tape == 2) __syncwarp();
+        tape2();
+    }
+    flush_record();
+    const double sum_m = __dadd_rn(cs->sum_m, static_cast<double>(sum_i));
+#pragma unroll
+    for (int u = 0; u < PPL; ++u)
+        if (t0 + u < k) insf[t0 + u] = hv[u];
+    __syncwarp();
+    if (lane == 0) {
+        cs->step = stp;
+        cs->L = Lb;
+        cs->E = E;
+        cs->best_E = bestE;
+        cs->sum_m = sum_m;
+        cs->flips += nflip;
+        cs->saturated += nsat;
+        c.sc[0] = len;
+        c.sc[1] += nrec;
+    }
+    __syncwarp();
+    return period_end;
+}
+
 template <typename QT, typename HT>
 __global__ void __launch_bounds__(512) pns_block_kernel(const __grid_constant__ KParams P) {
     using A = Arith<HT>;
@@ -717,8 +1009,8 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const __grid_constant__ 
         while (true) {
             bool done;
             const int ppl = block_ppl(k);
-            if (ppl == 1) done = block_period<QT, HT, 1>(P, bc);
-            else if (ppl == 2) done = block_period<QT, HT, 2>(P, bc);
+            if (ppl == 1) done = block_period_pipe<QT, HT, 1>(P, bc);
+            else if (ppl == 2) done = block_period_pipe<QT, HT, 2>(P, bc);
             else done = block_period<QT, HT, 4>(P, bc);
             if (done) break;
             // a full log (more than BLOCK_LOG moves in the period, L0 > BLOCK_LOG):

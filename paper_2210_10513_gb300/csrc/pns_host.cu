@@ -382,7 +382,9 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
                 // period: the wide-set form (4 positions per lane, k > 62)
                 // takes about three times as long per record as one position
                 // per lane, and runs fewer records per period.
-                const double wf[3] = {1.0, 1.5, 3.0};
+                double wf[3] = {1.0, 1.5, 3.0};
+                if (const char *e = getenv("PNS_FORM_WEIGHTS"))
+                    if (sscanf(e, "%lf,%lf,%lf", &wf[0], &wf[1], &wf[2]) != 3) wf[0] = 1.0, wf[1] = 1.5, wf[2] = 3.0;
                 double wsum = 0.0;
                 for (int f = 0; f < 3; ++f) wsum += wf[f] * static_cast<double>(ncls[f]);
                 const int64_t spare = S - msum;

@@ -139,6 +139,9 @@ struct pns_ctx {
     int64_t g_steps = -1;
     cudaStream_t g_stream = nullptr;
     bool tape_off = false;  // autotuner probes run without the tape
+    // pns_moments working memory, kept between calls (grow only)
+    void *d_mom = nullptr;
+    size_t mom_bytes = 0;
 };
 
 namespace {
@@ -148,7 +151,7 @@ void free_ctx(pns_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void *ptrs[] = {c->d_q, c->d_rowptr, c->d_col, c->d_diag, c->d_b, c->d_betas, c->d_inst, c->d_chain,
                     c->d_state, c->d_x, c->d_fields, c->d_cta, c->d_cta_chains, c->d_status, c->d_tape_flip,
-                    c->d_tape_m,  c->d_tape_x, c->d_tape_E, c->d_xbest, c->d_wtab, c->d_wtab_desc};
+                    c->d_tape_m,  c->d_tape_x, c->d_tape_E, c->d_xbest, c->d_wtab, c->d_wtab_desc, c->d_mom};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -1436,21 +1439,20 @@ pns_status pns_moments(pns_ctx *c, int32_t instance, int32_t beta_idx, pns_momen
     const int64_t recs = c->tape_cap;
     const int n = ih.n;
     const size_t scratch_bytes = moments_scratch_bytes(recs * static_cast<int64_t>(ids.size()), n);
-    int32_t *d_ids = nullptr;
-    void *d_scratch = nullptr;
-    double *d_out = nullptr;
-    struct Free {
-        void **a, **b, **c;
-        ~Free() {
-            if (*a) cudaFree(*a);
-            if (*b) cudaFree(*b);
-            if (*c) cudaFree(*c);
-        }
-    } fr{reinterpret_cast<void **>(&d_ids), &d_scratch, reinterpret_cast<void **>(&d_out)};
-    CU_MALLOC(&d_ids, sizeof(int32_t) * ids.size());
-    CU_MALLOC(&d_scratch, scratch_bytes);
     const size_t out_elems = 4 + 2 * static_cast<size_t>(n) + 2 * static_cast<size_t>(n) * n;
-    CU_MALLOC(&d_out, sizeof(double) * out_elems);
+    const size_t ids_bytes = (sizeof(int32_t) * ids.size() + 255) & ~static_cast<size_t>(255);
+    const size_t need = ids_bytes + ((scratch_bytes + 255) & ~static_cast<size_t>(255)) + sizeof(double) * out_elems;
+    if (c->mom_bytes < need) {
+        if (c->d_mom) CU(cudaFree(c->d_mom));
+        c->d_mom = nullptr;
+        c->mom_bytes = 0;
+        CU_MALLOC(&c->d_mom, need);
+        c->mom_bytes = need;
+    }
+    int32_t *d_ids = static_cast<int32_t *>(c->d_mom);
+    void *d_scratch = static_cast<char *>(c->d_mom) + ids_bytes;
+    double *d_out = reinterpret_cast<double *>(static_cast<char *>(d_scratch) +
+                                               ((scratch_bytes + 255) & ~static_cast<size_t>(255)));
     CU(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, s));
     double *o_sc = d_out, *o_x = d_out + 4, *o_xx = o_x + n, *o_ex = o_xx + n * n, *o_exx = o_ex + n;
     CU(launch_moments(c->d_tape_x, c->d_tape_m, c->d_tape_E, d_ids, static_cast<int64_t>(ids.size()), c->tape_cap,

@@ -6,14 +6,17 @@
 //     G0 = X^T diag(M) X,        G1 = X^T diag(M (E - c)) X
 // over S samples x_s in {0,1}^n.  These are dense contractions over the
 // sample axis, run on the 5th-generation tensor cores: tcgen05.mma with
-// bf16 operands in shared memory and fp32 accumulators in tensor memory.
-// Bits are exact in bf16; each weight is split into three bf16 parts
-// (w = w1 + w2 + w3, 24 significant bits), and the three parts of M and of
-// M (E - c) form six A-operand planes, two per 128-row MMA.  Multiplicities up
-// to 255 are exact in the first part, and each CTA accumulates at most 16384
-// samples in fp32 before its partial result is summed in fp64, so G0 is exact
-// for them; the energy-weighted sums carry an fp32 accumulation error of about
-// 2^-24 sqrt(16384) sum|w| / W relative to Cov.  The energy-weighted matrix is centred at c = <E> to avoid
+// bf16 operands and fp32 accumulators in tensor memory.  Bits are exact in
+// bf16; each weight is split into three bf16 parts (w = w1 + w2 + w3, 24
+// significant bits), and the three parts of M and of M (E - c) form six
+// weighted-bit planes of 64 rows, two per 128-row MMA.  The weighted planes
+// (the A operand) are written straight into tensor memory by the threads
+// that form them, so shared memory carries only the bit tile (the B operand).
+// Multiplicities up to 255 are exact in the first part, and fp32
+// accumulation runs over at most 16384 samples before it is added into an
+// fp64 partial, so G0 is exact for them; the energy-weighted sums carry an
+// fp32 accumulation error of about 2^-24 sqrt(16384) sum|w| / W relative to
+// Cov.  The energy-weighted matrix is centred at c = <E> to avoid
 // cancellation.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -25,17 +28,24 @@
 namespace pnsk {
 namespace {
 
-constexpr int MOM_N = 64;             // n <= 64 (rows of one plane)
-constexpr int STAGE_K = 64;           // samples per pipeline stage (four K = 16 slabs)
-constexpr int SAMPLES_PER_CTA = 16384;
-constexpr int A_SLAB_BYTES = 128 * 16 * 2;  // 128 rows x 16 bf16
-constexpr int B_SLAB_BYTES = 64 * 16 * 2;   // 64 rows x 16 bf16
-constexpr int STAGE_BYTES = 3 * 4 * A_SLAB_BYTES + 4 * B_SLAB_BYTES;  // 56 KiB
-constexpr int NBUF = 1;               // stage buffers per CTA (two CTAs share an SM and overlap)
-constexpr int MOM_SMEM = NBUF * STAGE_BYTES + 2048;
-constexpr int TMEM_COLS = 256;        // three 64-column fp32 accumulators
+constexpr int MOM_N = 64;                       // n <= 64: one 32-bit word of bits per row half
+constexpr int ST_SAMPLES = 32;                  // samples per stage (two K = 16 slabs)
+constexpr int SUB_STAGES = 512;                 // stages per fp32 accumulation run (16384 samples)
+constexpr int NGRP = 4;                         // builder warpgroups; stage g is built by group g mod 4
+constexpr int BUILD_THREADS = NGRP * 128;
+constexpr int NISSUE = 3;                        // issuing warps, one per accumulator (weight part)
+constexpr int MOM_THREADS = BUILD_THREADS + 32 * NISSUE;
+constexpr int B_SLAB_BYTES = 64 * 16 * 2;        // 64 rows x 16 bf16
+constexpr int B_STAGE_BYTES = 2 * B_SLAB_BYTES;
+constexpr int WPL_OFF = NGRP * B_STAGE_BYTES;    // weight parts per builder warp: [16][3][32] bf16
+constexpr int BAR_OFF = WPL_OFF + 16 * 3 * 32 * 2;
+constexpr int MOM_SMEM = BAR_OFF + 128;
+constexpr int TMEM_COLS = 512;
+constexpr uint32_t A_COL0 = 192;                 // accumulators in columns 0..191; A stages after them
+constexpr int MAX_MOM_CTAS = 160;
+constexpr int PART_DOUBLES = 2 * 64 * 64;        // per-CTA fp64 partial of G0 and G1
+constexpr int SUM_BLOCKS = 1216;                 // blocks of the fp64 scalar pass (8 per SM of 152)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
-constexpr int MOM_THREADS = 512;      // 16 warps build the operand tiles
 
 // Shared-memory matrix descriptor (no swizzle, K-major core matrices of 8 rows
 // x 16 bytes): start address, K-direction core-matrix stride (leading byte
@@ -57,7 +67,9 @@ __device__ __forceinline__ uint32_t saddr_of(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase; gives up early once another thread of
+// the CTA has raised `fail`.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int32_t *fail) {
     for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
         uint32_t ok;
         asm volatile(
@@ -66,12 +78,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 255u) == 255u && fail && *fail) return false;
     }
     return false;
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(float f) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // w ~ w1 + w2 + w3, each a bf16
@@ -86,6 +99,14 @@ __device__ __forceinline__ void split3(float w, uint16_t *o) {
     o[2] = __bfloat16_as_ushort(c);
 }
 
+// Byte permute with the sign-replicating selector form: a selector nibble
+// with bit 3 set gives 0xFF or 0x00 from the top bit of the chosen byte.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
 struct SampleSrc {
     const uint32_t *tape_x;  // W words per record
     const double *tape_m;
@@ -97,33 +118,58 @@ struct SampleSrc {
     int W;
 };
 
-__device__ __forceinline__ int64_t sample_row(const SampleSrc &src, int64_t s) {
-    const int64_t ci = s / src.recs;
-    const int64_t q = s - ci * src.recs;
-    return static_cast<int64_t>(src.chain_ids[ci]) * src.cap + q;
-}
+// Walks the samples s, s + stride, s + 2 stride, ... of the chain-major
+// sample order (sample s = record s mod recs of chain s / recs) without a
+// division per step.
+// Chain indices and record numbers fit 32 bits (the host checks recs).
+struct SampleWalk {
+    int64_t s, row_base;
+    int32_t ci, q, adv_c, adv_q, row_ci;
+    __device__ void init(const SampleSrc &src, int64_t s0, int64_t stride) {
+        s = s0;
+        const int64_t c0 = s0 / src.recs;
+        ci = static_cast<int32_t>(c0);
+        q = static_cast<int32_t>(s0 - c0 * src.recs);
+        adv_c = static_cast<int32_t>(stride / src.recs);
+        adv_q = static_cast<int32_t>(stride - static_cast<int64_t>(adv_c) * src.recs);
+        row_ci = -1;
+        row_base = 0;
+    }
+    __device__ __forceinline__ int64_t row(const SampleSrc &src) {
+        if (ci != row_ci) {
+            row_ci = ci;
+            row_base = static_cast<int64_t>(src.chain_ids[ci]) * src.cap;
+        }
+        return row_base + q;
+    }
+    __device__ __forceinline__ void next(const SampleSrc &src, int64_t stride) {
+        s += stride;
+        q += adv_q;
+        ci += adv_c;
+        if (q >= src.recs) {
+            q -= static_cast<int32_t>(src.recs);
+            ++ci;
+        }
+    }
+};
 
 // ---------------------------------------------------------------------------
-// fp64 sums over the samples: W = sum M, sum M E (pass 0); with the centre c:
-// sum M (E - c), sum M (E - c)^2 (pass 1).  Fixed grid and block: the
-// summation order, hence the result, is reproducible.
+// fp64 sums over the samples: W = sum M and sum M E.  Fixed grid and block:
+// the summation order, hence the result, is reproducible.
 // ---------------------------------------------------------------------------
-__global__ void scalar_sums_kernel(SampleSrc src, const double *centre, double *partials) {
+__global__ void __launch_bounds__(256) scalar_sums_kernel(SampleSrc src, double *partials) {
     __shared__ double sh[2][256];
     double a = 0.0, b = 0.0;
-    const double c = centre ? *centre : 0.0;
-    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < src.samples;
-         s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t row = sample_row(src, s);
-        const double m = src.tape_m[row];
-        const double e = src.tape_E[row];
-        if (centre) {
-            const double d = e - c;
-            a += m * d;
-            b += m * d * d;
-        } else {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t s0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s0 < src.samples) {
+        SampleWalk it;
+        it.init(src, s0, stride);
+        for (; it.s < src.samples; it.next(src, stride)) {
+            const int64_t row = it.row(src);
+            const double m = src.tape_m[row];
             a += m;
-            b += m * e;
+            b += m * src.tape_E[row];
         }
     }
     sh[0][threadIdx.x] = a;
@@ -142,50 +188,153 @@ __global__ void scalar_sums_kernel(SampleSrc src, const double *centre, double *
     }
 }
 
-// out[0..1] = sums of the partials in block order; with `centre_out` set,
-// also c = out[1] / out[0].
-__global__ void scalar_final_kernel(const double *partials, int blocks, double *out, double *centre_out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// out[0..1] = the sums of `count` partial pairs, in a fixed order (strided
+// per thread, then a tree); with `centre_out` set, also c = out[1] / out[0].
+__global__ void __launch_bounds__(256) scalar_final_kernel(const double *partials, int count, double *out,
+                                                           double *centre_out) {
+    __shared__ double sh[2][256];
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < blocks; ++i) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
         a += partials[2 * i];
         b += partials[2 * i + 1];
     }
-    out[0] = a;
-    out[1] = b;
-    if (centre_out) *centre_out = a > 0.0 ? b / a : 0.0;
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0];
+        out[1] = sh[1][0];
+        if (centre_out) *centre_out = sh[0][0] > 0.0 ? sh[1][0] / sh[0][0] : 0.0;
+    }
+}
+
+// The MMA issue loop of issuer m (one thread), kept out of line so that its
+// registers are allocated apart from the builders'.
+__device__ __noinline__ void issue_mmas(int m, unsigned char *sm, uint32_t tmem, int nst, int nsub, uint64_t *full,
+                                        uint64_t *empty, uint64_t *accbar, uint64_t *accfree, uint64_t *drain,
+                                        volatile int32_t *fail) {
+    uint32_t ta[NGRP][2], idesc, td;
+    uint64_t bd[NGRP][2];
+#pragma unroll
+    for (int u = 0; u < NGRP; ++u)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            asm volatile("mov.b32 %0, %1;" : "=r"(ta[u][t]) : "r"(tmem + A_COL0 + static_cast<uint32_t>(48 * u + 16 * m + 8 * t)));
+            asm volatile("mov.b64 %0, %1;" : "=l"(bd[u][t])
+                         : "l"(smem_desc(saddr_of(sm + u * B_STAGE_BYTES + t * B_SLAB_BYTES), 128, 256)));
+        }
+    asm volatile("mov.b32 %0, %1;" : "=r"(idesc) : "n"(kIdesc));
+    asm volatile("mov.b32 %0, %1;" : "=r"(td) : "r"(tmem + static_cast<uint32_t>(64 * m)));
+    for (int sub = 0; sub < nsub && !*fail; ++sub) {
+        const int g0 = sub * SUB_STAGES;
+        const int g1 = min(nst, g0 + SUB_STAGES);
+        if (sub > 0 && !mbar_wait(saddr_of(accfree), static_cast<uint32_t>((sub - 1) & 1), fail)) {
+            *fail = 1;
+            break;
+        }
+        bool bad = false;
+        for (int g = g0; g < g1 && !bad; g += NGRP) {
+#pragma unroll
+            for (int u = 0; u < NGRP; ++u) {
+                if (bad || g + u >= g1) continue;
+                if (!mbar_wait(saddr_of(&full[u]), static_cast<uint32_t>(((g + u) >> 2) & 1), fail)) {
+                    bad = true;
+                    continue;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (g + u == g0)
+                    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 0;" ::"r"(td),
+                                 "r"(ta[u][0]), "l"(bd[u][0]), "r"(idesc)
+                                 : "memory");
+                else
+                    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 1;" ::"r"(td),
+                                 "r"(ta[u][0]), "l"(bd[u][0]), "r"(idesc)
+                                 : "memory");
+                asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 1;" ::"r"(td),
+                             "r"(ta[u][1]), "l"(bd[u][1]), "r"(idesc)
+                             : "memory");
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        saddr_of(&empty[u]))
+                    : "memory");
+            }
+        }
+        if (bad) {
+            *fail = 1;
+            break;
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         saddr_of(accbar))
+                     : "memory");
+    }
+    if (*fail) {
+        // let this issuer's MMAs still in flight finish before the columns are freed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         saddr_of(&drain[m]))
+                     : "memory");
+        mbar_wait(saddr_of(&drain[m]), 0u, nullptr);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// The tensor-core contraction.  512 threads; each CTA takes up to 16384
-// samples in stages of 64.  All 16 warps build a stage's operand tiles (the
-// build, not the MMA, sets the pace); with NBUF = 1 stage buffer a CTA needs
-// 58 KiB, so two CTAs share an SM and one builds while the other's MMAs run.
+// The tensor-core contraction.  One CTA per SM, each over a contiguous range
+// of samples, in stages of 32.  Warp w < 16 is a builder: warpgroup u = w / 4
+// builds the stages g = u (mod 4), and its warp of lane quarter q = w mod 4
+// owns TMEM lanes 32 q .. 32 q + 31, i.e. bit row i = 32 (q mod 2) + lane of
+// the planes of half h = q / 2 (h = 0: the parts of M, h = 1: the parts of
+// M (E - c)).  For its 32 samples a builder warp
+//   * loads one sample per lane (two stages ahead) and splits its weight,
+//   * transposes the 32 x 32 bit block so that lane i holds row i's bits,
+//   * turns each pair of bits into a 32-bit mask and ANDs it with the bf16
+//     pairs of the three weight parts, storing them into TMEM (tcgen05.st),
+//   * (h = 0) stores the bits as bf16 1.0 / 0 into the shared-memory B tile.
+// Warps 16, 17, 18 issue the MMAs: warp 16 + m, for accumulator m, waits for
+// each stage in order and issues the two MMAs of weight part m (K = 16 slabs;
+// A from TMEM, B from shared memory).  Two or more issuers keep the tensor
+// pipe full with N = 64 MMAs, which one issuing thread does not.
+// Every 512 stages the builders add the fp32 accumulators into the CTA's
+// fp64 partial and the next run starts from zero.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(MOM_THREADS, 3 - NBUF) moments_tc_kernel(SampleSrc src, const double *centre, float *partials,
-                                                            int32_t *status) {
+__global__ void __launch_bounds__(MOM_THREADS, 1)
+    moments_tc_kernel(SampleSrc src, const double *centre, double *part, double *spart, int32_t *status) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *const stage_base = sm;
-    uint16_t *planes = reinterpret_cast<uint16_t *>(sm + NBUF * STAGE_BYTES);       // [6][64]
-    uint32_t *bits_t = reinterpret_cast<uint32_t *>(sm + NBUF * STAGE_BYTES + 1024);  // [64 rows][2]: bit s = sample s
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + NBUF * STAGE_BYTES + 1536);  // [NBUF]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + NBUF * STAGE_BYTES + 1552);
-    int32_t *fail = reinterpret_cast<int32_t *>(sm + NBUF * STAGE_BYTES + 1556);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + BAR_OFF);  // [4]: a stage built (128 arrivals)
+    uint64_t *empty = full + 4;                                   // [4]: its MMAs done (commit)
+    uint64_t *accbar = full + 8;                                  // a run's MMAs done (commit)
+    uint64_t *accfree = full + 9;                                 // the run's accumulators read out
+    uint64_t *drain = full + 10;                                  // [3]: an issuer's MMAs done (failure path)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + BAR_OFF + 104);
+    volatile int32_t *fail = reinterpret_cast<volatile int32_t *>(sm + BAR_OFF + 108);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const int64_t s_begin = static_cast<int64_t>(blockIdx.x) * SAMPLES_PER_CTA;
-    int64_t s_end = s_begin + SAMPLES_PER_CTA;
-    if (s_end > src.samples) s_end = src.samples;
-    const int stages = static_cast<int>((s_end - s_begin + STAGE_K - 1) / STAGE_K);
-    const double c = *centre;
+    const int lane = tid & 31;
+    const int64_t S = src.samples;
+    const int64_t beg = S * blockIdx.x / gridDim.x;
+    const int64_t end = S * (blockIdx.x + 1) / gridDim.x;
+    const int nst = static_cast<int>((end - beg + ST_SAMPLES - 1) / ST_SAMPLES);
+    const int nsub = (nst + SUB_STAGES - 1) / SUB_STAGES;
 
     if (tid == 0) {
-        for (int b = 0; b < NBUF; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr_of(&mbar[b])) : "memory");
+        for (int u = 0; u < NGRP; ++u) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr_of(&full[u])), "r"(128) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr_of(&empty[u])), "r"(NISSUE) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr_of(accbar)), "r"(NISSUE) : "memory");
+        for (int m = 0; m < NISSUE; ++m)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr_of(&drain[m])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr_of(accfree)), "r"(BUILD_THREADS)
+                     : "memory");
         *fail = 0;
     }
-    if (warp == 0) {
+    if (warp == 16) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr_of(tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
@@ -196,199 +345,214 @@ __global__ void __launch_bounds__(MOM_THREADS, 3 - NBUF) moments_tc_kernel(Sampl
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    // One sample per thread of the first 64, held in registers one stage
-    // ahead so that its global loads overlap the build of the current stage.
-    double nx_m = 0.0, nx_e = 0.0;
-    uint32_t nx_x0 = 0u, nx_x1 = 0u;
-    bool nx_valid = false;
-    auto load_sample = [&](int g) {
-        const int64_t s = s_begin + static_cast<int64_t>(g) * STAGE_K + tid;
-        nx_valid = g < stages && s < s_end;
-        if (nx_valid) {
-            const int64_t row = sample_row(src, s);
-            nx_m = src.tape_m[row];
-            nx_e = src.tape_E[row];
-            nx_x0 = src.tape_x[row * src.W];
-            nx_x1 = src.W > 1 ? src.tape_x[row * src.W + 1] : 0u;
-        }
-    };
-    if (tid < STAGE_K) load_sample(0);
-    int committed = 0;  // stages whose MMAs were issued
-    for (int g = 0; g < stages; ++g) {
-        const int buf = g % NBUF;
-        unsigned char *sb = stage_base + buf * STAGE_BYTES;
-        if (g >= NBUF) {
-            // the MMAs of stage g - NBUF read this buffer
-            if (!mbar_wait(saddr_of(&mbar[buf]), static_cast<uint32_t>(((g - NBUF) / NBUF) & 1))) {
-                if (tid == 0) *fail = 1;
-            }
-        }
-        __syncthreads();
-        if (*fail) break;
-        // stage the 64 samples (loaded during the previous stage): six weight
-        // planes and the bits; then start the loads of the next stage
-        if (tid < STAGE_K) {
-            uint16_t pw[6] = {0, 0, 0, 0, 0, 0};
-            if (nx_valid) {
-                split3(static_cast<float>(nx_m), pw);
-                split3(static_cast<float>(nx_m * (nx_e - c)), pw + 3);
-            }
-            for (int p = 0; p < 6; ++p) planes[p * STAGE_K + tid] = pw[p];
-            // the bits transposed: row i's word w holds bit i of samples
-            // 32 w .. 32 w + 31.  Each warp transposes its two 32 x 32 bit
-            // blocks (lane = sample, bit = row) by the recursive block swap:
-            // at size j, a lane with bit j clear keeps its columns with bit j
-            // clear and takes its partner's (lane + j) same columns moved up
-            // by j; the partner keeps the others and takes the rest moved
-            // down.  Afterwards lane l holds rows l and l + 32.
-            uint32_t r0 = nx_valid ? nx_x0 : 0u, r1 = nx_valid ? nx_x1 : 0u;
-            const int ln = tid & 31;
+    if (warp >= 16) {
+        // Issuer m = warp - 16 owns accumulator m: for every stage in order it
+        // issues the two MMAs (K = 16 slabs) of weight part m.  Its operands
+        // sit in registers written once: a tcgen05.mma keeps reading its
+        // register operands while it runs, so a register rewritten for the
+        // next MMA would wait for the previous one to finish.
+        if (lane == 0) issue_mmas(warp - 16, sm, tmem, nst, nsub, full, empty, accbar, accfree, drain, fail);
+        __syncwarp();
+    } else {
+        const int u = warp >> 2;
+        const int q = warp & 3;
+        const int h = q >> 1;
+        const int wi = q & 1;
+        const int row = 32 * wi + lane;
+        const double c = *centre;
+        double *prow = part + (static_cast<int64_t>(blockIdx.x) * 2 + h) * 64 * 64 + row * 64 + 16 * u;
 #pragma unroll
-            for (int j = 16; j >= 1; j >>= 1) {
-                const uint32_t m = j == 16 ? 0x0000FFFFu
-                                   : j == 8 ? 0x00FF00FFu
-                                   : j == 4 ? 0x0F0F0F0Fu
-                                   : j == 2 ? 0x33333333u
-                                            : 0x55555555u;
-                const uint32_t p0 = __shfl_xor_sync(0xFFFFFFFFu, r0, j);
-                const uint32_t p1 = __shfl_xor_sync(0xFFFFFFFFu, r1, j);
-                const bool low = (ln & j) == 0;
-                r0 = low ? ((r0 & m) | ((p0 & m) << j)) : ((r0 & ~m) | ((p0 & ~m) >> j));
-                r1 = low ? ((r1 & m) | ((p1 & m) << j)) : ((r1 & ~m) | ((p1 & ~m) >> j));
+        for (int k = 0; k < 16; ++k) prow[k] = 0.0;
+        uint16_t *wp = reinterpret_cast<uint16_t *>(sm + WPL_OFF) + warp * 96;
+        const uint32_t tq = tmem + (static_cast<uint32_t>(32 * q) << 16);
+        double sa = 0.0, sb = 0.0;  // q == 2: sum M (E - c), sum M (E - c)^2
+
+        // this lane's sample of stage g = u + 4 j is beg + 32 g + lane
+        constexpr int64_t STRIDE = NGRP * ST_SAMPLES;
+        SampleWalk it;
+        it.init(src, beg + ST_SAMPLES * u + lane, STRIDE);
+        auto fetch = [&](double &fm, double &fe, uint32_t &fx) {
+            if (it.s < end) {
+                const int64_t r = it.row(src);
+                fm = src.tape_m[r];
+                fe = src.tape_E[r];
+                fx = wi < src.W ? src.tape_x[r * src.W + wi] : 0u;
+            } else {
+                fm = 0.0;
+                fe = 0.0;
+                fx = 0u;
             }
-            bits_t[2 * ln + (tid >> 5)] = r0;
-            bits_t[2 * (ln + 32) + (tid >> 5)] = r1;
-            load_sample(g + 1);
-        }
-        __syncthreads();
-        // A chunks: (mma m, row r, octet o) -> 8 bf16 along the sample axis
-        for (int cidx = tid; cidx < 3 * 128 * 8; cidx += MOM_THREADS) {
-            const int m = cidx / (128 * 8);
-            const int rem = cidx - m * 128 * 8;
-            const int r = rem >> 3;
-            const int o = rem & 7;
-            const int i = r & 63;
-            const int p = 2 * m + (r >> 6);
-            // samples 8 o .. 8 o + 7: their bits of row i (one byte) mask the
-            // plane's eight weights (one 16-byte read)
-            const uint32_t byte = (bits_t[2 * i + (o >> 2)] >> (8 * (o & 3))) & 0xFFu;
-            const uint4 w8 = *reinterpret_cast<const uint4 *>(planes + p * STAGE_K + 8 * o);
-            const uint32_t wv[4] = {w8.x, w8.y, w8.z, w8.w};
-            uint32_t packed[4];
+            it.next(src, STRIDE);
+        };
+        // two stages in flight, in two register sets used alternately, so
+        // that no register copy waits for a load
+        double mA, eA, mB, eB;
+        uint32_t xA, xB;
+        fetch(mA, eA, xA);
+        fetch(mB, eB, xB);
+        // one stage of this group: consumes the set (pm, pe, px), refills it
+        // with the stage two ahead, builds the A parts and the B tile
+        auto build_stage = [&](int j, double &pm, double &pe, uint32_t &px) -> bool {
+            float wv;
+            if (h == 0) {
+                wv = static_cast<float>(pm);
+            } else {
+                const double d = pe - c;
+                wv = static_cast<float>(pm * d);
+                if (q == 2) {
+                    sa += pm * d;
+                    sb += pm * d * d;
+                }
+            }
+            const uint32_t x = px;
+            fetch(pm, pe, px);  // stage j + 2
+            uint16_t p3[3];
+            split3(wv, p3);
+            __syncwarp();
+            wp[lane] = p3[0];
+            wp[32 + lane] = p3[1];
+            wp[64 + lane] = p3[2];
+            // transpose: lane i gets row i's bits (bit s = sample s)
+            uint32_t xr = x;
 #pragma unroll
-            for (int e2 = 0; e2 < 4; ++e2) {
-                const uint32_t two = byte >> (2 * e2);
-                const uint32_t mask = ((two & 1u) * 0x0000FFFFu) | (((two >> 1) & 1u) * 0xFFFF0000u);
-                packed[e2] = wv[e2] & mask;
+            for (int jj = 16; jj >= 1; jj >>= 1) {
+                const uint32_t mk = jj == 16 ? 0x0000FFFFu
+                                    : jj == 8 ? 0x00FF00FFu
+                                    : jj == 4 ? 0x0F0F0F0Fu
+                                    : jj == 2 ? 0x33333333u
+                                              : 0x55555555u;
+                const uint32_t p = __shfl_xor_sync(0xFFFFFFFFu, xr, jj);
+                xr = (lane & jj) == 0 ? ((xr & mk) | ((p & mk) << jj)) : ((xr & ~mk) | ((p & ~mk) >> jj));
             }
-            const int slab = o >> 1;
-            const int off = m * 4 * A_SLAB_BYTES + slab * A_SLAB_BYTES + (r >> 3) * 256 + (o & 1) * 128 + (r & 7) * 16;
-            *reinterpret_cast<uint4 *>(sb + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        }
-        // B chunks: (row j, octet o) -> bits as bf16 1.0 / 0
-        for (int cidx = tid; cidx < 64 * 8; cidx += MOM_THREADS) {
-            const int j = cidx >> 3;
-            const int o = cidx & 7;
-            const uint32_t byte = (bits_t[2 * j + (o >> 2)] >> (8 * (o & 3))) & 0xFFu;
-            uint32_t packed[4];
+            // masks: word e covers samples 2e (low half) and 2e + 1.  Each
+            // nibble of bits is spread to the top bits of four bytes
+            // (multiplying by 0x10204081 places bit k at bit 8 k + 7,
+            // without overlapping terms), which the sign-replicating
+            // byte permute widens to 16-bit masks.
+            uint32_t mw[16];
+            const uint32_t xe = xr & 0x0F0F0F0Fu;
+            const uint32_t xo = (xr >> 4) & 0x0F0F0F0Fu;
 #pragma unroll
-            for (int e2 = 0; e2 < 4; ++e2) {
-                const uint32_t two = byte >> (2 * e2);
-                const uint32_t mask = ((two & 1u) * 0x0000FFFFu) | (((two >> 1) & 1u) * 0xFFFF0000u);
-                packed[e2] = 0x3F803F80u & mask;  // bf16 1.0 where the bit is set
+            for (int nb = 0; nb < 8; ++nb) {
+                const uint32_t nib = prmt((nb & 1) ? xo : xe, 0u, 0x4440u | static_cast<uint32_t>(nb >> 1));
+                const uint32_t sp = nib * 0x10204081u;
+                mw[2 * nb] = prmt(sp, 0u, 0x9988u);
+                mw[2 * nb + 1] = prmt(sp, 0u, 0xBBAAu);
             }
-            const int slab = o >> 1;
-            const int off = 3 * 4 * A_SLAB_BYTES + slab * B_SLAB_BYTES + (j >> 3) * 256 + (o & 1) * 128 + (j & 7) * 16;
-            *reinterpret_cast<uint4 *>(sb + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        }
-        // make the generic-proxy writes visible to the tensor cores
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+            __syncwarp();
+            // the MMAs of this group's previous stage read the buffers
+            if (j > 0) {
+                const bool w_ok = mbar_wait(saddr_of(&empty[u]), static_cast<uint32_t>((j - 1) & 1), fail);
+                if (!__all_sync(0xFFFFFFFFu, w_ok)) {
+                    *fail = 1;
+                    return false;
+                }
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = saddr_of(sb);
-            for (int slab = 0; slab < 4; ++slab) {
-                const uint64_t bdesc = smem_desc(base + 3 * 4 * A_SLAB_BYTES + slab * B_SLAB_BYTES, 128, 256);
-                for (int m = 0; m < 3; ++m) {
-                    const uint64_t adesc = smem_desc(base + m * 4 * A_SLAB_BYTES + slab * A_SLAB_BYTES, 128, 256);
-                    const uint32_t acc = (g > 0 || slab > 0) ? 1u : 0u;
-                    const uint32_t dt = tmem + static_cast<uint32_t>(m * 64);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {  // slab t: words 8 t .. 8 t + 7
+                    const uint4 *wk = reinterpret_cast<const uint4 *>(wp + 32 * k + 16 * t);
+                    const uint4 wa = wk[0], wb = wk[1];
+                    const uint32_t *mt = mw + 8 * t;
+                    const uint32_t ta = tq + A_COL0 + static_cast<uint32_t>(48 * u + 16 * k + 8 * t);
                     asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-                        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+                        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta),
+                        "r"(wa.x & mt[0]), "r"(wa.y & mt[1]), "r"(wa.z & mt[2]), "r"(wa.w & mt[3]),
+                        "r"(wb.x & mt[4]), "r"(wb.y & mt[5]), "r"(wb.z & mt[6]), "r"(wb.w & mt[7])
                         : "memory");
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             saddr_of(&mbar[buf]))
-                         : "memory");
-        }
-        committed = g + 1;
-    }
-    // wait for the MMAs of the last (up to two) committed stages
-    for (int g = committed - NBUF; g < committed; ++g) {
-        if (g < 0) continue;
-        if (!mbar_wait(saddr_of(&mbar[g % NBUF]), static_cast<uint32_t>((g / NBUF) & 1))) {
-            if (tid == 0) *fail = 1;
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool ok = *fail == 0 && committed == stages;
-    if (ok) {
-        // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows of the
-        // accumulators); the four warps of a lane quarter split the columns
-        const int quarter = warp & 3;
-        const int lane_row = 32 * quarter + (tid & 31);
-        float *dst = partials + static_cast<int64_t>(blockIdx.x) * 3 * 128 * 64;
-        for (int blk = warp >> 2; blk < 12; blk += MOM_THREADS / 128) {
-            const int m = blk >> 2;
-            const int c0 = (blk & 3) * 16;
-            {
-                uint32_t v[16];
-                const uint32_t ta = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(m * 64 + c0);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(ta)
-                    : "memory");
+            if (h == 0) {
+                unsigned char *bb = sm + u * B_STAGE_BYTES + (row >> 3) * 256 + (row & 7) * 16;
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const uint32_t one = 0x3F803F80u;  // bf16 1.0 in both halves
+                    *reinterpret_cast<uint4 *>(bb + (o >> 1) * B_SLAB_BYTES + (o & 1) * 128) =
+                        make_uint4(mw[4 * o] & one, mw[4 * o + 1] & one, mw[4 * o + 2] & one,
+                                   mw[4 * o + 3] & one);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(saddr_of(&full[u]));
+            return true;
+        };
+        int j = 0;  // this group's stage count
+        bool ok = true;
+        for (int sub = 0; sub < nsub && ok; ++sub) {
+            const int g0 = sub * SUB_STAGES;
+            const int g1 = min(nst, g0 + SUB_STAGES);
+            for (int g = g0 + u; g < g1; g += NGRP, ++j) {
+                const bool r = (j & 1) == 0 ? build_stage(j, mA, eA, xA) : build_stage(j, mB, eB, xB);
+                if (!r) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!ok) break;
+            // the run's accumulators: this warp's lanes, columns 16 u .. 16 u + 15 of each part
+            const bool w_ok = mbar_wait(saddr_of(accbar), static_cast<uint32_t>(sub & 1), fail);
+            if (!__all_sync(0xFFFFFFFFu, w_ok)) {
+                *fail = 1;
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int hc = 0; hc < 2; ++hc) {  // columns 16 u + 8 hc .. + 7
+                uint32_t d[3][8];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const uint32_t ta = tq + static_cast<uint32_t>(64 * m + 16 * u + 8 * hc);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                 : "=r"(d[m][0]), "=r"(d[m][1]), "=r"(d[m][2]), "=r"(d[m][3]), "=r"(d[m][4]),
+                                   "=r"(d[m][5]), "=r"(d[m][6]), "=r"(d[m][7])
+                                 : "r"(ta)
+                                 : "memory");
+                }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float *row = dst + (static_cast<int64_t>(m) * 128 + lane_row) * 64 + c0;
-                for (int q = 0; q < 16; ++q) row[q] = __uint_as_float(v[q]);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    prow[8 * hc + k] += (static_cast<double>(__uint_as_float(d[0][k])) +
+                                         static_cast<double>(__uint_as_float(d[1][k]))) +
+                                        static_cast<double>(__uint_as_float(d[2][k]));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(saddr_of(accfree));
+        }
+        if (q == 2) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                sa += __shfl_xor_sync(0xFFFFFFFFu, sa, o);
+                sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+            }
+            if (lane == 0) {
+                spart[2 * (blockIdx.x * NGRP + u)] = sa;
+                spart[2 * (blockIdx.x * NGRP + u) + 1] = sb;
             }
         }
-    } else if (tid == 0) {
-        atomicCAS(status, 0, ST_TIMEOUT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (tid == 0 && *fail) atomicCAS(status, 0, ST_TIMEOUT);
+    if (warp == 16) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
-// G_g[i][j] = sum over CTAs (in order) of the three planes of group g, fp64.
-// Planes 0..5 = (mma, row half) (0,0) (0,1) (1,0) | (1,1) (2,0) (2,1).
-__global__ void reduce_planes_kernel(const float *partials, int ctas, int n, double *G0, double *G1) {
+// G_h[i][j] = sum over CTAs (in order) of the fp64 partials.
+__global__ void reduce_parts_kernel(const double *part, int ctas, int n, double *G0, double *G1) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 2 * n * n) return;
     const int g = idx / (n * n);
     const int rem = idx - g * n * n;
     const int i = rem / n, j = rem - (rem / n) * n;
     double acc = 0.0;
-    for (int b = 0; b < ctas; ++b) {
-        const float *pb = partials + static_cast<int64_t>(b) * 3 * 128 * 64;
-        for (int q = 0; q < 3; ++q) {
-            const int plane = 3 * g + q;
-            const int m = plane >> 1, half = plane & 1;
-            acc += static_cast<double>(pb[(static_cast<int64_t>(m) * 128 + half * 64 + i) * 64 + j]);
-        }
-    }
+    for (int b = 0; b < ctas; ++b) acc += part[(static_cast<int64_t>(b) * 2 + g) * 64 * 64 + i * 64 + j];
     (g == 0 ? G0 : G1)[i * n + j] = acc;
 }
 
@@ -444,15 +608,16 @@ __global__ void grads_kernel(int n, float beta, const double *scalars, const dou
 // Host entry points (internal; the C ABI wrappers live in pns_host.cu).
 // ---------------------------------------------------------------------------
 size_t moments_scratch_bytes(int64_t samples, int n) {
-    const int64_t ctas = (samples + SAMPLES_PER_CTA - 1) / SAMPLES_PER_CTA;
-    return static_cast<size_t>(ctas) * 3 * 128 * 64 * 4 + 2 * static_cast<size_t>(n) * n * 8 + 4096 * 8 + 64 * 8;
+    (void)samples;
+    return static_cast<size_t>(MAX_MOM_CTAS) * PART_DOUBLES * 8 + 2 * static_cast<size_t>(n) * n * 8 +
+           (2 * SUM_BLOCKS + 2 * NGRP * MAX_MOM_CTAS + 8) * 8;
 }
 
 cudaError_t launch_moments(const uint32_t *tape_x, const double *tape_m, const double *tape_E,
                            const int32_t *chain_ids, int64_t chains, int64_t cap, int64_t recs, int W, int n,
                            void *scratch, int32_t *status, double *scalars, double *mean_x, double *mean_xx,
                            double *cov_ex, double *cov_exx, cudaStream_t s) {
-    if (n < 1 || n > MOM_N || W < 1) return cudaErrorInvalidValue;
+    if (n < 1 || n > MOM_N || W < 1 || recs < 0 || recs > INT32_MAX || chains > INT32_MAX) return cudaErrorInvalidValue;
     SampleSrc src;
     src.tape_x = tape_x;
     src.tape_m = tape_m;
@@ -460,34 +625,43 @@ cudaError_t launch_moments(const uint32_t *tape_x, const double *tape_m, const d
     src.chain_ids = chain_ids;
     src.cap = cap;
     src.recs = recs;
-    src.samples = chains * recs;
+    src.samples = recs > 0 ? chains * recs : 0;
     src.W = W;
-    const int64_t ctas = (src.samples + SAMPLES_PER_CTA - 1) / SAMPLES_PER_CTA;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM, each over at least 2048 samples
+    int64_t ctas = (src.samples + 2047) / 2048;
+    if (ctas > sms) ctas = sms;
+    if (ctas > MAX_MOM_CTAS) ctas = MAX_MOM_CTAS;
     char *p = static_cast<char *>(scratch);
-    float *partials = reinterpret_cast<float *>(p);
-    p += static_cast<size_t>(ctas) * 3 * 128 * 64 * 4;
+    double *part = reinterpret_cast<double *>(p);
+    p += static_cast<size_t>(MAX_MOM_CTAS) * PART_DOUBLES * 8;
     double *G0 = reinterpret_cast<double *>(p);
     double *G1 = G0 + n * n;
-    double *sp = G1 + n * n;   // 4096 doubles of scalar partials
-    double *s0 = sp + 4096;    // [2]
-    double *s1 = s0 + 2;       // [2]
-    double *centre = s1 + 2;   // [1]
-    const int sb = 512;
-    scalar_sums_kernel<<<sb, 256, 0, s>>>(src, nullptr, sp);
-    scalar_final_kernel<<<1, 32, 0, s>>>(sp, sb, s0, centre);
-    scalar_sums_kernel<<<sb, 256, 0, s>>>(src, centre, sp);
-    scalar_final_kernel<<<1, 32, 0, s>>>(sp, sb, s1, nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    double *sp0 = G1 + n * n;              // [SUM_BLOCKS][2]
+    double *sp1 = sp0 + 2 * SUM_BLOCKS;    // [ctas][NGRP][2]
+    double *s0 = sp1 + 2 * NGRP * MAX_MOM_CTAS;  // [2]
+    double *s1 = s0 + 2;                   // [2]
+    double *centre = s1 + 2;               // [1]
     if (src.samples > 0) {
-        const int smem = MOM_SMEM;
+        scalar_sums_kernel<<<SUM_BLOCKS, 256, 0, s>>>(src, sp0);
+        scalar_final_kernel<<<1, 256, 0, s>>>(sp0, SUM_BLOCKS, s0, centre);
+        // one CTA per SM: ask for more shared memory than two CTAs could share
+        const int smem = MOM_SMEM > (116 << 10) ? MOM_SMEM : (116 << 10);
         e = cudaFuncSetAttribute(moments_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        moments_tc_kernel<<<static_cast<unsigned>(ctas), MOM_THREADS, smem, s>>>(src, centre, partials, status);
+        moments_tc_kernel<<<static_cast<unsigned>(ctas), MOM_THREADS, smem, s>>>(src, centre, part, sp1, status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        scalar_final_kernel<<<1, 256, 0, s>>>(sp1, static_cast<int>(ctas) * NGRP, s1, nullptr);
+    } else {
+        ctas = 0;
+        e = cudaMemsetAsync(s0, 0, 5 * sizeof(double), s);
+        if (e != cudaSuccess) return e;
     }
-    reduce_planes_kernel<<<(2 * n * n + 127) / 128, 128, 0, s>>>(partials, static_cast<int>(ctas), n, G0, G1);
+    reduce_parts_kernel<<<(2 * n * n + 127) / 128, 128, 0, s>>>(part, static_cast<int>(ctas), n, G0, G1);
     assemble_kernel<<<(n * n + 127) / 128, 128, 0, s>>>(n, G0, G1, s0, s1, centre, static_cast<double>(src.samples),
                                                         scalars, mean_x, mean_xx, cov_ex, cov_exx);
     return cudaGetLastError();

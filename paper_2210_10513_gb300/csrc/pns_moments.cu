@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(MOM_THREADS, 1)
         for (int k = 0; k < 16; ++k) prow[k] = 0.0;
         uint16_t *wp = reinterpret_cast<uint16_t *>(sm + WPL_OFF) + warp * 96;
         const uint32_t tq = tmem + (static_cast<uint32_t>(32 * q) << 16);
-        double sa = 0.0, sb = 0.0;  // q == 2: sum M (E - c), sum M (E - c)^2
+        double sa = 0.0, sb = 0.0;  // q == 2: sum M (E - c); q == 3: sum M (E - c)^2
 
         // this lane's sample of stage g = u + 4 j is beg + 32 g + lane
         constexpr int64_t STRIDE = NGRP * ST_SAMPLES;
@@ -398,11 +398,14 @@ __global__ void __launch_bounds__(MOM_THREADS, 1)
                 wv = static_cast<float>(pm);
             } else {
                 const double d = pe - c;
-                wv = static_cast<float>(pm * d);
-                if (q == 2) {
-                    sa += pm * d;
-                    sb += pm * d * d;
-                }
+                const double md = pm * d;
+                wv = static_cast<float>(md);
+                // the fp64 pipe is narrow: the two scalar sums go to the two
+                // warps of this half, which sit on different schedulers
+                if (q == 2)
+                    sa += md;
+                else
+                    sb = fma(md, d, sb);
             }
             const uint32_t x = px;
             fetch(pm, pe, px);  // stage j + 2
@@ -523,16 +526,11 @@ __global__ void __launch_bounds__(MOM_THREADS, 1)
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(saddr_of(accfree));
         }
-        if (q == 2) {
+        if (h == 1) {
+            double v = q == 2 ? sa : sb;
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                sa += __shfl_xor_sync(0xFFFFFFFFu, sa, o);
-                sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
-            }
-            if (lane == 0) {
-                spart[2 * (blockIdx.x * NGRP + u)] = sa;
-                spart[2 * (blockIdx.x * NGRP + u) + 1] = sb;
-            }
+            for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            if (lane == 0) spart[2 * (blockIdx.x * NGRP + u) + (q - 2)] = v;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const __grid_constant__ 
 
     extern __shared__ __align__(16) unsigned char smem[];
     const CtaDesc cd = P.cta[blockIdx.x];
-    const int W = P.gw;
+    const int W = cd.pad > 0 ? cd.pad : P.gw;  // warps per group (the layout keeps the launch's P.gw)
     const int R = P.R;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -893,7 +893,7 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const __grid_constant__ 
     const int k = in.k;
     const int kp = (k + 3) & ~3;  // sub-block row stride and padded set length
     const QT *Q = reinterpret_cast<const QT *>(in.q);
-    const BlockSmem L = block_smem(ld, k, static_cast<int32_t>(sizeof(HT)), static_cast<int32_t>(sizeof(QT)), R, W);
+    const BlockSmem L = block_smem(ld, k, static_cast<int32_t>(sizeof(HT)), static_cast<int32_t>(sizeof(QT)), R, P.gw);
     unsigned char *gbase = smem + chd0.smem_off;
     auto area = [&](int s) { return gbase + s * L.chain_bytes; };
     auto cst = [&](int s) { return reinterpret_cast<ChainState *>(area(s) + L.state); };

@@ -365,6 +365,8 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
         // shared out over the forms in proportion to their groups.
         if (const char *e = getenv("PNS_FORM_PER_SM"); !e || atoi(e)) {
             const int S = num_sms;
+            const char *ew = getenv("PNS_WIDE_GROUPS");
+            const bool wide_groups = !ew || atoi(ew);
             std::vector<int> ucls(units.size());
             int64_t ncls[3] = {0, 0, 0};
             for (size_t i = 0; i < units.size(); ++i) {
@@ -454,7 +456,14 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
                         d.first = static_cast<int32_t>(o.cta_chains.size());
                         d.count = 0;
                         d.groups = static_cast<int32_t>(members[b2].size());
+                        // wide-set CTAs (4 positions per lane, no draw
+                        // buffers) give each group the CTA's spare warps, up
+                        // to one warp per chain
                         d.pad = 0;
+                        if (wide_groups && ucls[members[b2][0]] == 2) {
+                            const int wcta = std::min(R, (cap_units * wpg) / d.groups);
+                            if (wcta > wpg) d.pad = wcta;
+                        }
                         size_t off = 0;
                         for (int ui : members[b2]) {
                             const Unit &u = units[ui];

@@ -45,7 +45,7 @@ struct CtaDesc {
     int32_t first;          // first entry in the CTA chain list
     int32_t count;          // chains (teams) in this CTA
     int32_t groups;         // exchange groups in this CTA (count / R when exchanging)
-    int32_t pad;
+    int32_t pad;            // period-blocked kernel: warps per group in this CTA (0: the launch's)
 };
 
 // Persistent per-chain state in global memory (96 bytes).

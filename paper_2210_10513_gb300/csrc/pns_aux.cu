@@ -70,6 +70,102 @@ __global__ void prepare_dense_kernel(const QT *q, int n, int ld, const QT *b_raw
     }
 }
 
+__device__ __forceinline__ void acc_add(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ double ld_cg_acc(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ long long ld_cg_acc(const long long *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg_q(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ int32_t ld_cg_q(const int32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ int16_t ld_cg_q(const int16_t *p) { return __ldcg(p); }
+__device__ __forceinline__ void acc_add(long long *p, long long v) {  // v >= 0
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+
+// Tiled form for pns_create: block (I, J), J >= I, compares the 32 x 32 tile
+// (I, J) with the transpose of tile (J, I), both read row-wise through
+// shared memory from src (row pitch sld); adds each row's |q| into rowsum
+// (the tile's rows of I and, off the diagonal, of J); when src is a packed
+// copy (src != q), writes both tiles into q (row pitch ld); zeroes q's
+// padding columns n .. ld - 1 (last column tile).  Every element is read
+// twice, coalesced.  The last block to finish (a counter in `done`) forms
+// the row bounds, their finiteness and diag / b.  fp32 rows are summed over
+// a tile in fp32 (an overflow reads as a non-finite bound, which is rejected
+// like a bound over the limit) and across tiles in fp64.
+template <typename QT>
+__global__ void __launch_bounds__(256)
+    prepare_tiles_kernel(const QT *src, int sld, QT *q, int ld, int n, const QT *b_raw,
+                         typename Mirror<QT>::Acc *rowsum, unsigned int *done, typename Mirror<QT>::C *diag_out,
+                         typename Mirror<QT>::C *b_out, int32_t *flags, unsigned long long *bound) {
+    using C = typename Mirror<QT>::C;
+    using Acc = typename Mirror<QT>::Acc;
+    using Red = typename std::conditional<std::is_same<QT, float>::value, float, long long>::type;
+    const int I = blockIdx.y, J = blockIdx.x;
+    if (J < I) return;
+    __shared__ QT A[32][33], B[32][33];
+    __shared__ bool last;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int ca = J * 32 + tx, cb = I * 32 + tx;
+    for (int r = ty; r < 32; r += 8) {
+        const int ra = I * 32 + r, rb = J * 32 + r;
+        A[r][tx] = ra < n && ca < n ? src[static_cast<int64_t>(ra) * sld + ca] : QT(0);
+        B[r][tx] = rb < n && cb < n ? src[static_cast<int64_t>(rb) * sld + cb] : QT(0);
+    }
+    __syncthreads();
+    int32_t f = 0;
+    for (int r = ty; r < 32; r += 8) {
+        const QT a = A[r][tx], t = B[tx][r], b = B[r][tx];
+        if (bits_of(a) != bits_of(t)) f |= FLAG_ASYM;
+        if (!finite_v(a) || !finite_v(b)) f |= FLAG_NONFINITE;
+        // row sums: warp ty adds row r's |A| and |B| over its lanes
+        Red sa = a < QT(0) ? -static_cast<Red>(a) : static_cast<Red>(a);
+        Red sb = b < QT(0) ? -static_cast<Red>(b) : static_cast<Red>(b);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            sa += __shfl_xor_sync(0xFFFFFFFFu, sa, o);
+            sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+        }
+        if (tx == 0) {
+            if (I * 32 + r < n) acc_add(&rowsum[I * 32 + r], static_cast<Acc>(sa));
+            if (I != J && J * 32 + r < n) acc_add(&rowsum[J * 32 + r], static_cast<Acc>(sb));
+        }
+    }
+    if (f) atomicOr(flags, f);
+    if (src != q) {  // a packed copy: both tiles into the pitched matrix
+        for (int r = ty; r < 32; r += 8) {
+            const int ra = I * 32 + r, rb = J * 32 + r;
+            if (ra < n && ca < n) q[static_cast<int64_t>(ra) * ld + ca] = A[r][tx];
+            if (I != J && rb < n && cb < n) q[static_cast<int64_t>(rb) * ld + cb] = B[r][tx];
+        }
+    }
+    if (J == static_cast<int>(gridDim.x) - 1) {
+        for (int r = ty; r < 32; r += 8) {
+            const int ra = I * 32 + r;
+            if (ra < n && ca >= n && ca < ld) q[static_cast<int64_t>(ra) * ld + ca] = QT(0);
+        }
+    }
+    // the last block to finish: every tile's sums and writes are in
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int T = gridDim.x;
+        last = atomicAdd(done, 1u) == T * (T + 1) / 2 - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const QT bi = b_raw ? b_raw[i] : QT(0);
+        Acc tot = ld_cg_acc(&rowsum[i]);
+        if (!finite_v(bi)) atomicOr(flags, FLAG_NONFINITE);
+        tot += bi < QT(0) ? -static_cast<Acc>(bi) : static_cast<Acc>(bi);
+        if constexpr (std::is_same<QT, float>::value) {
+            if (!isfinite(tot)) atomicOr(flags, FLAG_NONFINITE);
+        }
+        atomic_max_bound(bound, tot);
+        diag_out[i] = static_cast<C>(ld_cg_q(&q[static_cast<int64_t>(i) * ld + i]));
+        b_out[i] = static_cast<C>(bi);
+    }
+}
+
 // One thread per row of a CSR matrix (values already int32 or float).
 template <typename VT>
 __global__ void prepare_csr_kernel(const int32_t *row_ptr, const int32_t *col, const VT *val, const VT *diag_raw,
@@ -251,6 +347,32 @@ cudaError_t init_csr_t(const InstDesc *inst, const ChainDesc *chain, const uint3
 }
 
 }  // namespace
+
+namespace {
+template <typename QT>
+cudaError_t prepare_tiled_t(const void *src, int sld, void *q, int n, int ld, const void *b_raw, void *diag_out,
+                            void *b_out, void *rowsum, int32_t *flags, unsigned long long *bound, cudaStream_t s) {
+    using C = typename Mirror<QT>::C;
+    using Acc = typename Mirror<QT>::Acc;
+    const int T = (n + 31) / 32;
+    prepare_tiles_kernel<QT><<<dim3(T, T), 256, 0, s>>>(
+        static_cast<const QT *>(src), sld, static_cast<QT *>(q), ld, n, static_cast<const QT *>(b_raw),
+        static_cast<Acc *>(rowsum), reinterpret_cast<unsigned int *>(static_cast<Acc *>(rowsum) + n),
+        static_cast<C *>(diag_out), static_cast<C *>(b_out), flags, bound);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_prepare_dense_tiled(int qtype, const void *src, int sld, void *q, int n, int ld, const void *b_raw,
+                                       void *diag_out, void *b_out, void *rowsum, int32_t *flags,
+                                       unsigned long long *bound, cudaStream_t s) {
+    switch (qtype) {
+    case 0: return prepare_tiled_t<int16_t>(src, sld, q, n, ld, b_raw, diag_out, b_out, rowsum, flags, bound, s);
+    case 1: return prepare_tiled_t<int32_t>(src, sld, q, n, ld, b_raw, diag_out, b_out, rowsum, flags, bound, s);
+    case 2: return prepare_tiled_t<float>(src, sld, q, n, ld, b_raw, diag_out, b_out, rowsum, flags, bound, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_prepare_dense(int qtype, const void *q, int n, int ld, const void *b_raw, void *diag_out,
                                  void *b_out, int32_t *flags, unsigned long long *bound, cudaStream_t s) {

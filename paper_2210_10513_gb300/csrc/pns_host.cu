@@ -967,7 +967,28 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
     const size_t q_bytes = static_cast<size_t>(std::max<int64_t>(q_elems, 1)) * (c->fmt == PNS_DENSE ? qb : vb);
     CU_MALLOC(&c->d_q, q_bytes);
     c->q_bytes = q_bytes;
-    CU(cudaMemsetAsync(c->d_q, 0, q_bytes, s));
+    // (dense: the tiled check zeroes the padding columns; nothing else is unwritten)
+    if (c->fmt != PNS_DENSE) CU(cudaMemsetAsync(c->d_q, 0, q_bytes, s));
+    // Dense instances arrive packed (row pitch n) through a transient staging
+    // copy of them all: one plain copy per instance, then the tiled check
+    // writes them into the pitched layout.  Without room for it, each is
+    // copied pitched (a 2D copy) and checked in place.
+    void *d_stage = nullptr;
+    struct StageFree {
+        void **p;
+        ~StageFree() {
+            if (*p) cudaFree(*p);
+        }
+    } stagefree{&d_stage};
+    if (c->fmt == PNS_DENSE) {
+        int64_t st_elems = 0;
+        for (const InstHost &ih : c->inst) st_elems += static_cast<int64_t>(ih.n) * ih.n;
+        if (cudaMalloc(&d_stage, static_cast<size_t>(std::max<int64_t>(st_elems, 1)) * qb) != cudaSuccess) {
+            (void)cudaGetLastError();
+            d_stage = nullptr;
+        }
+    }
+    int64_t st_off = 0;
     CU_MALLOC(&c->d_diag, static_cast<size_t>(vec_elems) * vb);
     CU_MALLOC(&c->d_b, static_cast<size_t>(vec_elems) * vb);
     CU(cudaMemsetAsync(c->d_diag, 0, static_cast<size_t>(vec_elems) * vb, s));
@@ -997,26 +1018,100 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
         max_n = std::max<int64_t>(max_n, ih.n);
         max_nnz = std::max<int64_t>(max_nnz, ih.nnz);
     }
-    // scratch for raw b / diag / CSR values of one instance at a time
-    const size_t tmp_bytes = static_cast<size_t>(std::max<int64_t>({2 * max_n, max_nnz, 1})) * 4 + 64;
+    // scratch: dense, every instance's raw b and row sums side by side (no
+    // reuse, so no wait between instances); CSR, raw b / diag / values of
+    // one instance at a time
+    const size_t tmp_bytes = c->fmt == PNS_DENSE ? static_cast<size_t>(vec_elems) * (4 + 8) + 8 * n_probs + 64
+                                                 : static_cast<size_t>(std::max<int64_t>({2 * max_n, max_nnz, 1})) * 4 + 64;
     CU_MALLOC(&d_tmp, tmp_bytes);
     char *tmp = static_cast<char *>(d_tmp);
+    // the ladders: device ones copied each, host ones gathered and copied in
+    // runs of consecutive instances
+    {
+        std::vector<char> on_dev(n_probs, 0);
+        std::vector<float> hb(static_cast<size_t>(beta_elems), 0.0f);
+        for (int p = 0; p < n_probs; ++p) {
+            const InstHost &ih = c->inst[p];
+            cudaPointerAttributes pa{};
+            on_dev[p] = cudaPointerGetAttributes(&pa, probs[p].betas) == cudaSuccess &&
+                        (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+            (void)cudaGetLastError();
+            if (on_dev[p])
+                CU(cudaMemcpyAsync(c->d_betas + ih.beta_off, probs[p].betas, sizeof(float) * ih.R, cudaMemcpyDefault,
+                                   s));
+            else
+                memcpy(hb.data() + ih.beta_off, probs[p].betas, sizeof(float) * ih.R);
+        }
+        for (int p = 0; p < n_probs;) {
+            if (on_dev[p]) {
+                ++p;
+                continue;
+            }
+            int q = p;
+            while (q + 1 < n_probs && !on_dev[q + 1]) ++q;
+            const int64_t o = c->inst[p].beta_off, e = c->inst[q].beta_off + c->inst[q].R;
+            CU(cudaMemcpy(c->d_betas + o, hb.data() + o, sizeof(float) * (e - o), cudaMemcpyHostToDevice));
+            p = q + 1;
+        }
+    }
+    if (c->fmt == PNS_DENSE)
+        CU(cudaMemsetAsync(tmp + static_cast<size_t>(vec_elems) * 4, 0,
+                           static_cast<size_t>(vec_elems) * 8 + 8 * n_probs, s));
+    // dense: the copies on a copy stream, back to back, in 8 batches of
+    // instances; each batch's checks (on s) wait only for its own copies
+    std::vector<int64_t> st_at(n_probs, 0);
+    constexpr int NB = 8;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev[NB] = {};
+    struct CopyStreamFree {
+        cudaStream_t *cs;
+        cudaEvent_t *ev;
+        ~CopyStreamFree() {
+            for (int i = 0; i < NB; ++i)
+                if (ev[i]) cudaEventDestroy(ev[i]);
+            if (*cs) cudaStreamDestroy(*cs);
+        }
+    } csfree{&cstream, ev};
+    auto batch_of = [&](int p) { return static_cast<int>(static_cast<int64_t>(p) * NB / n_probs); };
+    if (c->fmt == PNS_DENSE) {
+        CU(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking));
+        for (int i = 0; i < NB; ++i) CU(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+        CU(cudaEventRecord(ev[0], s));  // (the copies follow the memsets above)
+        CU(cudaStreamWaitEvent(cstream, ev[0], 0));
+        for (int p = 0; p < n_probs; ++p) {
+            const pns_problem &pr = probs[p];
+            const InstHost &ih = c->inst[p];
+            char *qd = static_cast<char *>(c->d_q) + ih.q_off * qb;
+            if (d_stage) {
+                st_at[p] = st_off;
+                st_off += static_cast<int64_t>(ih.n) * ih.n;
+                CU(cudaMemcpyAsync(static_cast<char *>(d_stage) + st_at[p] * qb, pr.q,
+                                   static_cast<size_t>(ih.n) * ih.n * qb, cudaMemcpyDefault, cstream));
+            } else {
+                CU(cudaMemcpy2DAsync(qd, static_cast<size_t>(ih.ld) * qb, pr.q, static_cast<size_t>(ih.n) * qb,
+                                     static_cast<size_t>(ih.n) * qb, ih.n, cudaMemcpyDefault, cstream));
+            }
+            if (pr.b)
+                CU(cudaMemcpyAsync(tmp + static_cast<size_t>(ih.vec_off) * 4, pr.b, static_cast<size_t>(ih.n) * qb,
+                                   cudaMemcpyDefault, cstream));
+            if (p + 1 == n_probs || batch_of(p + 1) != batch_of(p)) CU(cudaEventRecord(ev[batch_of(p)], cstream));
+        }
+    }
     for (int p = 0; p < n_probs; ++p) {
         const pns_problem &pr = probs[p];
         const InstHost &ih = c->inst[p];
-        CU(cudaMemcpyAsync(c->d_betas + ih.beta_off, pr.betas, sizeof(float) * ih.R, cudaMemcpyDefault, s));
         char *diag_out = static_cast<char *>(c->d_diag) + ih.vec_off * vb;
         char *b_out = static_cast<char *>(c->d_b) + ih.vec_off * vb;
         if (c->fmt == PNS_DENSE) {
+            if (p == 0 || batch_of(p) != batch_of(p - 1)) CU(cudaStreamWaitEvent(s, ev[batch_of(p)], 0));
             char *qd = static_cast<char *>(c->d_q) + ih.q_off * qb;
-            CU(cudaMemcpy2DAsync(qd, static_cast<size_t>(ih.ld) * qb, pr.q, static_cast<size_t>(ih.n) * qb,
-                                 static_cast<size_t>(ih.n) * qb, ih.n, cudaMemcpyDefault, s));
-            const void *braw = nullptr;
-            if (pr.b) {
-                CU(cudaMemcpyAsync(tmp, pr.b, static_cast<size_t>(ih.n) * qb, cudaMemcpyDefault, s));
-                braw = tmp;
-            }
-            CU(launch_prepare_dense(c->qtype, qd, ih.n, ih.ld, braw, diag_out, b_out, d_flags + p, d_bound + p, s));
+            const void *src = d_stage ? static_cast<const void *>(static_cast<char *>(d_stage) + st_at[p] * qb) : qd;
+            const int sld = d_stage ? ih.n : ih.ld;
+            const void *braw = pr.b ? tmp + static_cast<size_t>(ih.vec_off) * 4 : nullptr;
+            // instance p's row sums, then its block counter (8 bytes per instance apart)
+            void *rowsum = tmp + static_cast<size_t>(vec_elems) * 4 + static_cast<size_t>(ih.vec_off) * 8 + 8 * p;
+            CU(launch_prepare_dense_tiled(c->qtype, src, sld, qd, ih.n, ih.ld, braw, diag_out, b_out, rowsum,
+                                          d_flags + p, d_bound + p, s));
         } else {
             CU(cudaMemcpyAsync(c->d_rowptr + ih.rp_off, pr.row_ptr, sizeof(int32_t) * (ih.n + 1), cudaMemcpyDefault, s));
             char *vals = static_cast<char *>(c->d_q) + ih.q_off * vb;
@@ -1037,14 +1132,18 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
             CU(launch_prepare_csr(c->is_float, c->d_rowptr + ih.rp_off, c->d_col + ih.q_off, vals, diag_out, b_out,
                                   ih.n, ih.nnz, diag_out, b_out, d_flags + p, d_bound + p, s));
         }
-        // the scratch buffer is reused by the next instance
-        CU(cudaStreamSynchronize(s));
+        // (CSR: the scratch buffer is reused by the next instance)
+        if (c->fmt != PNS_DENSE) CU(cudaStreamSynchronize(s));
     }
     std::vector<int32_t> flags(n_probs);
     std::vector<unsigned long long> bound(n_probs);
     CU(cudaMemcpyAsync(flags.data(), d_flags, sizeof(int32_t) * n_probs, cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(bound.data(), d_bound, sizeof(unsigned long long) * n_probs, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (d_stage) {
+        CU(cudaFree(d_stage));
+        d_stage = nullptr;
+    }
     long long ibound = 0;
     for (int p = 0; p < n_probs; ++p) {
         if (flags[p] & FLAG_BAD_CSR) return fail(PNS_ERR_INVALID_ARG, "problem %d: malformed CSR structure", p);
@@ -1061,9 +1160,9 @@ pns_status pns_create(const pns_problem *probs, int32_t n_probs, const pns_confi
             ibound = std::max(ibound, v);
         }
     }
-    for (const InstHost &ih : c->inst) {
-        std::vector<float> b(ih.R);
-        CU(cudaMemcpy(b.data(), c->d_betas + ih.beta_off, sizeof(float) * ih.R, cudaMemcpyDeviceToHost));
+    {
+        std::vector<float> b(static_cast<size_t>(beta_elems));
+        CU(cudaMemcpy(b.data(), c->d_betas, sizeof(float) * b.size(), cudaMemcpyDeviceToHost));
         for (float v : b)
             if (!(v >= 0.0f) || !(v < 3.0e38f)) return fail(PNS_ERR_INVALID_ARG, "betas must be finite and >= 0");
     }
@@ -1311,6 +1410,16 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
         if (c->spec > 0) return launch_spec(c->qtype, c->spec, Pl, grid, c->n_threads, c->smem, s);
         return launch_sampler(c->fmt, c->qtype, c->hbytes, c->T, Pl, grid, c->n_threads, c->smem, s);
     };
+    if (P.tape && pt) {
+        // with exchange a run is counted in original samples, so chains make
+        // different numbers of records: the tape past a chain's records reads
+        // as zeros, not as an earlier run's entries
+        const size_t recs = static_cast<size_t>(c->tape_cap) * static_cast<size_t>(c->chains);
+        CU(cudaMemsetAsync(c->d_tape_flip, 0, sizeof(int32_t) * recs, s));
+        CU(cudaMemsetAsync(c->d_tape_m, 0, sizeof(double) * recs, s));
+        if (c->d_tape_x) CU(cudaMemsetAsync(c->d_tape_x, 0, sizeof(uint32_t) * c->W * recs, s));
+        if (c->d_tape_E) CU(cudaMemsetAsync(c->d_tape_E, 0, sizeof(double) * recs, s));
+    }
     if (!plain && c->cfg.graph && s != nullptr && !c->tape_off) {
         // one captured launch per step count; the chain state lives in device
         // memory, so replaying the same graph continues the chains

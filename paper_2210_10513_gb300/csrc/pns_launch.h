@@ -26,6 +26,14 @@ bool sampler_supported(int fmt, int qtype, int hbytes, int T);
 // flags.
 cudaError_t launch_prepare_dense(int qtype, const void *q, int n, int ld, const void *b_raw, void *diag_out,
                                  void *b_out, int32_t *flags, unsigned long long *bound, cudaStream_t s);
+// The same checks in 32 x 32 tiles (coalesced), for a matrix the library
+// owns (q, row pitch ld), read from src (row pitch sld): src == q checks in
+// place; otherwise src is a packed copy that is written into q.  Also
+// zeroes q's padding columns n .. ld - 1.  rowsum: scratch of n 8-byte
+// accumulators and one 4-byte counter after them, zeroed by the caller.
+cudaError_t launch_prepare_dense_tiled(int qtype, const void *src, int sld, void *q, int n, int ld, const void *b_raw,
+                                       void *diag_out, void *b_out, void *rowsum, int32_t *flags,
+                                       unsigned long long *bound, cudaStream_t s);
 // CSR instance set-up: values are stored as int32 or float already.
 cudaError_t launch_prepare_csr(int is_float, const int32_t *row_ptr, const int32_t *col, const void *val,
                                const void *diag_raw, const void *b_raw, int n, int64_t nnz, void *diag_out,

@@ -74,7 +74,8 @@ def tempering_config(n_inst, samples, world=1):
     return {"workload": tempering_desc(n_inst, samples), "instances": n_inst, "replicas": T_REPLICAS,
             "chains": n_inst * T_REPLICAS, "L0": T_L0, "swap_interval": T_SWAP, "samples_per_step": samples,
             "l2": "Q (3 GB) exceeds L2; a 256 MiB buffer is also written between timed steps",
-            "parallelism": "instances sharded by n^2 over %d rank(s)" % world}
+            "parallelism": "%d instances per GPU: %d instances sharded by n^2 over %d rank(s), no data-path "
+                           "collective" % (n_inst // world, n_inst, world)}
 
 
 def peaks():
@@ -195,7 +196,8 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean(times) * 1e3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": tempering_config(args.instances, args.samples),
+            "config": tempering_config(args.instances * max(1, int(os.environ.get("WORLD_SIZE", "1"))), args.samples,
+                                       max(1, int(os.environ.get("WORLD_SIZE", "1")))),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"], "single_core_value": last["single_core_rate"]},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -294,7 +296,9 @@ def tempering_arm(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)  # non-default stream: pns_run replays a captured CUDA graph
     torch.cuda.set_stream(stream)
-    n_inst = args.instances
+    # weak scaling: `--instances` instances per GPU, all of them sharded over
+    # the ranks by n^2 (at N = 1 the 512 of the single-GPU workload)
+    n_inst = args.instances * world
     samples = args.samples
     ns_all = synth.tempering_sizes(n_inst, args.seed)
     lo, hi = shard.shard_instances([n * n * T_REPLICAS for n in ns_all], world, rank)

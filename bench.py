@@ -17,9 +17,10 @@ oracle timed on the host cores (`cpu_baseline`), the one-group-per-launch
 form (`batched_over_plain`) and, unless `--quick`, the dense int16 n = 1024
 workload's figures with its L2-side roofline (`dense1024`).
 
-With torchrun (N > 1) the instances are sharded across ranks by n^2 (whole
-exchange groups, no data-path collective); the value is the records of all
-ranks over the slowest rank's time.
+With torchrun (N > 1) the workload grows with N (`--instances` per GPU) and
+all N x 512 instances are sharded across ranks by n^2 (whole exchange groups,
+no data-path collective): weak scaling; the value is the records of all ranks
+over the slowest rank's time.
 
 `--impl reference` times the CPU oracle instead (a bounded sample of the same
 workload on the host cores).  `--workload dense1024|lattice|fit|donuts` prints
@@ -383,24 +384,32 @@ def tempering_arm(args):
     # create + run + read (states and statistics) per step
     q_host = [torch.from_numpy(q).pin_memory() for q in qs]
     h2d = int(sum(q.nbytes for q in qs) + 4 * T_REPLICAS * len(qs))
-    e_steps = max(2, min(args.steps, 4))
+    e_steps = max(2, min(args.steps, 6))
     t_e, recs_e, d2h = [], 0.0, 0
+    parts = np.zeros(4)  # create, run, read, destroy (host clock, summed over the timed steps)
     for i in range(e_steps + 1):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         se = make(q_host, seed=args.seed + 1000 + i)
+        ta = time.perf_counter()
         se.run(samples)
+        torch.cuda.current_stream().synchronize()
+        tb = time.perf_counter()
         out = se.read(tape=False)
+        tc = time.perf_counter()
         se.close()
         t2 = time.perf_counter()
         if i > 0:  # the first one warms the allocator and the module
             t_e.append(t2 - t1)
+            parts += [ta - t1, tb - ta, tc - tb, t2 - tc]
             recs_e += float(out["stats"]["steps"].sum())
             d2h = int(out["states"].nbytes + out["stats"].nbytes)
     e_tot = _allreduce(dist, [recs_e])[0]
     e_time = _allreduce(dist, [sum(t_e)], "max")[0]
     e2e = {"value": e_tot / e_time, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "ms_per_step": e_time / len(t_e) * 1e3}
+           "ms_per_step": e_time / len(t_e) * 1e3,
+           "split_ms": {k: float(v) / len(t_e) * 1e3 for k, v in zip(("create", "run", "read", "destroy"), parts)},
+           "steps": len(t_e)}
 
     if rank != 0:
         if dist is not None:

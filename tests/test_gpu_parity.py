@@ -322,3 +322,61 @@ def test_checkpoint_moves_between_kernel_forms(monkeypatch, src, dst):
     for key in ("states", "stats", "flips", "m"):
         np.testing.assert_array_equal(ra[key], rb[key], err_msg=key)
     np.testing.assert_array_equal(fa, fb)
+
+
+@pytest.mark.parametrize("case", ["asym_lower", "asym_upper", "asym_int16", "nan_lower", "b_inf", "range_int32",
+                                  "range_fp32", "valid"])
+def test_create_checks_span_tiles(case):
+    """pns_create's checks run in 32 x 32 tiles: n = 77 spans three tile rows
+    with a ragged last one.  A broken symmetry or a non-finite entry in any
+    tile, or a field bound reached only by summing a row over several tiles,
+    is rejected with the status of Sec. 4's input rules; a valid instance
+    passes."""
+    from paper_2210_10513_gb300 import pns
+    n = 77
+    q = synth.dense_int(n, -3, 3, 4, np.int32)
+    b = None
+    status = None
+    if case == "asym_lower":
+        q = q.copy()
+        q[70, 3] += 1
+        status = 2
+    elif case == "asym_upper":
+        q = q.copy()
+        q[3, 70] += 1
+        status = 2
+    elif case == "asym_int16":
+        q = q.astype(np.int16)
+        q[40, 66] += 1
+        status = 2
+    elif case == "nan_lower":
+        q = synth.dense_normal(n, 1.0, 4)
+        q[75, 40] = np.nan
+        status = 3
+    elif case == "b_inf":
+        q = synth.dense_normal(n, 1.0, 4)
+        b = synth.vector_normal(n, 1.0, 4)
+        b[76] = np.inf
+        status = 3
+    elif case == "range_int32":
+        # row 50: 77 entries of 1e7, each tile's part (32 e7) below the
+        # 715,827,882 limit, the whole row above it
+        q = q.copy()
+        q[50, :] = 10 ** 7
+        q[:, 50] = 10 ** 7
+        status = 3
+    elif case == "range_fp32":
+        q = synth.dense_normal(n, 1.0, 4)
+        q[40, :] = 2e28
+        q[:, 40] = 2e28
+        status = 3
+    prob = dict(n=n, q=q, b=b, betas=[1.0])
+    if status is None:
+        s = pns.Sampler([prob], variant="unbiased", k=7)
+        s.run(100)
+        assert s.read()["stats"]["steps"].min() == 100
+        s.close()
+        return
+    with pytest.raises(pns.PnsError) as ei:
+        pns.Sampler([prob], variant="unbiased", k=7)
+    assert ei.value.status == status, (case, ei.value.status)

@@ -156,6 +156,9 @@ typedef struct {
     int32_t set_sweep;         /* 1: set-sweep kernel (Unbiased PNS, systematic sets): the
                                   spec_depth warps of a chain evaluate every set of the current
                                   state once, then decide up to 32 * spec_depth records at once */
+    int32_t chains_per_warp;   /* 2: two chains per warp, one per half (Unbiased PNS on systematic
+                                  sets of k <= 16, no exchange, many chains); else 1 */
+    int32_t reserved_info;
 } pns_info;
 
 typedef struct {

@@ -99,6 +99,7 @@ struct pns_ctx {
     int spec = 0;  // > 0: speculative kernel with this many warps (records) per chain
     bool blocked = false;  // period-blocked kernel
     bool sweep = false;    // with spec > 0: the set-sweep kernel (spec warps per chain)
+    bool half = false;     // two chains per warp (pns_half.cu)
     int gw = 1;            // blocked kernel: warps per exchange group
     std::vector<InstHost> inst;
     int32_t max_ld = 32, LD = 32, W = 1;
@@ -269,11 +270,11 @@ static pns_status plan(const pns_ctx &c, const std::vector<ChainDesc> &chains, i
     const bool list = needs_list(c.cfg.variant, c.cfg.subset);
     const bool slot_list = c.prod > 0 && c.cfg.variant == PNS_BASIC;
     const bool pt = c.cfg.swap_interval > 0;
-    const int TT = 32 * (T + c.prod);
+    const int TT = c.half ? 16 : 32 * (T + c.prod);  // threads per chain
     // named barriers per CTA (ids 1..15): two per team when a team has more
     // than one warp, then one per exchange group
     const bool team_bars = TT > 32;
-    int teams_cap = T == 32 ? 1 : std::min(512 / TT, team_bars ? 7 : 16);
+    int teams_cap = T == 32 ? 1 : std::min(512 / TT, team_bars ? 7 : (c.half ? 32 : 16));
     if (c.spec > 0) teams_cap = std::max(1, std::min(512 / (32 * c.spec), 15));
     if (c.blocked) teams_cap = 16;
     struct Unit {
@@ -581,6 +582,7 @@ static int auto_warps(const pns_ctx &c) {
 struct Mapping {
     int T = 1, prod = 0, spec = 0, per_cta = 0, block = 0, gw = 0;  // gw 0: chosen by the planner
     int sweep = 0;  // with spec: the set-sweep kernel
+    int half = 0;   // two chains per warp
 };
 
 // The period-blocked kernel: Unbiased PNS, systematic sets, exchange, dense Q, k <= 128.
@@ -589,6 +591,15 @@ static bool block_allowed(const pns_ctx &c) {
     for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
     return c.fmt == PNS_DENSE && c.cfg.swap_interval > 0 && c.cfg.variant == PNS_UNBIASED && c.R <= 16 &&
            c.cfg.L0 < (1ll << 31) && c.cfg.subset == PNS_SUBSET_SYSTEMATIC && block_supported(c.qtype, kmax);
+}
+
+// Two chains per warp: Unbiased PNS on systematic sets of k <= 16, dense Q
+// with 4-byte fields, no exchange.
+static bool half_allowed(const pns_ctx &c) {
+    int kmax = 1;
+    for (const InstHost &ih : c.inst) kmax = std::max(kmax, ih.k);
+    return c.fmt == PNS_DENSE && c.hbytes == 4 && c.cfg.swap_interval == 0 && c.cfg.variant == PNS_UNBIASED &&
+           c.cfg.subset == PNS_SUBSET_SYSTEMATIC && kmax <= 16 && c.cfg.warps_per_chain <= 1;
 }
 
 static bool spec_allowed(const pns_ctx &c) {
@@ -660,6 +671,19 @@ static pns_status default_mapping(const pns_ctx &c, Mapping &m) {
         m.prod = 0;
         m.spec = 0;
     }
+    // Two chains per warp where many one-warp chains make the launch
+    // throughput-bound (more chains than 16 warps on every SM hold).
+    m.half = half_allowed(c) && m.T == 1 && m.prod == 0 && m.spec == 0 && !m.block &&
+                     c.chains > 16ll * c.num_sms
+                 ? 1
+                 : 0;
+    if (const char *e = getenv("PNS_HALF")) m.half = atoi(e) && half_allowed(c) && !m.block ? 1 : 0;
+    if (m.half) {
+        m.T = 1;
+        m.prod = 0;
+        m.spec = 0;
+        m.sweep = 0;
+    }
     return PNS_OK;
 }
 
@@ -675,6 +699,7 @@ static pns_status apply_mapping(pns_ctx *c, Mapping m, cudaStream_t s) {
         c->spec = m.spec;
         c->sweep = m.spec > 0 && m.sweep != 0;
         c->blocked = m.block != 0;
+        c->half = m.half != 0;
         pl = PlanOut();
         if (c->blocked) {
             // warps per group: the most (up to R) at which every CTA is resident
@@ -762,8 +787,10 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
                 if (!bar) continue;
                 if (std::string(line, bar - line) == key) {
                     Mapping m;
-                    if (sscanf(bar + 1, "%d %d %d %d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta, &m.block, &m.gw,
-                               &m.sweep) == 7) {
+                    const int got = sscanf(bar + 1, "%d %d %d %d %d %d %d %d", &m.T, &m.prod, &m.spec, &m.per_cta,
+                                           &m.block, &m.gw, &m.sweep, &m.half);
+                    if (got == 7 || got == 8) {
+                        if (got == 7 || !half_allowed(*c)) m.half = 0;
                         fclose(f);
                         return apply_mapping(c, m, s);
                     }
@@ -787,9 +814,10 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         if (m.sweep && (m.spec <= 0 || !sweep_allowed(*c, m.spec))) return;
         if (m.block && (!block_allowed(*c) || m.T != 1)) return;
         if ((c->cfg.track_best || c->cfg.anneal_steps > 0) && (m.block || m.spec > 0)) return;
+        if (m.half && (!half_allowed(*c) || m.T != 1 || m.prod || m.spec || m.block)) return;
         for (const Mapping &o : cands)
             if (o.T == m.T && o.prod == m.prod && o.spec == m.spec && o.per_cta == m.per_cta && o.block == m.block &&
-                o.gw == m.gw && o.sweep == m.sweep)
+                o.gw == m.gw && o.sweep == m.sweep && o.half == m.half)
                 return;
         cands.push_back(m);
     };
@@ -801,6 +829,9 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
         add(Mapping{1, 0, 8, c->per_cta, 0, 0, 1});
         if (c->per_cta == 0) add(Mapping{1, 0, 8, 1, 0, 0, 1});  // one chain per CTA: two CTAs share an SM
         for (int gw : {0, c->R, (c->R + 1) / 2, (c->R + 3) / 4}) add(Mapping{1, 0, 0, c->per_cta, 1, gw});
+        Mapping hm{1, 0, 0, c->per_cta};
+        hm.half = 1;
+        add(hm);
     } else {
         for (int T : Ts_csr) add(Mapping{T, 0, 0, c->per_cta});
     }
@@ -878,8 +909,8 @@ static pns_status autotune(pns_ctx *c, cudaStream_t s) {
     if (code != 0) return fail(static_cast<pns_status>(code), "device error while autotuning");
     if (path) {
         if (FILE *f = fopen(path, "a")) {
-            fprintf(f, "%s|%d %d %d %d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta, best.block,
-                    best.gw, best.sweep);
+            fprintf(f, "%s|%d %d %d %d %d %d %d %d\n", key.c_str(), best.T, best.prod, best.spec, best.per_cta,
+                    best.block, best.gw, best.sweep, best.half);
             fclose(f);
         }
     }
@@ -907,6 +938,8 @@ pns_status pns_get_info(const pns_ctx *ctx, pns_info *info) {
     info->spec_depth = ctx->spec;
     info->set_sweep = ctx->sweep ? 1 : 0;
     info->period_blocked = ctx->blocked ? 1 : 0;
+    info->chains_per_warp = ctx->half ? 2 : 1;
+    info->reserved_info = 0;
     return PNS_OK;
 }
 
@@ -1399,6 +1432,7 @@ static pns_status run_impl(pns_ctx *c, int64_t steps, void *stream, bool plain) 
     P.group_base = static_cast<uint32_t>(c->cfg.group_base);
     auto launch = [&](const KParams &Pl, int grid) -> cudaError_t {
         if (c->blocked) return launch_block(c->qtype, Pl, grid, c->n_threads, c->smem, s);
+        if (c->half) return launch_half(c->qtype, Pl, grid, c->n_threads, c->smem, s);
         if (c->spec > 0 && c->sweep) {
             int max_sets = 1, max_k = 1;
             for (const InstHost &ih : c->inst) {

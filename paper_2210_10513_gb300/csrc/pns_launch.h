@@ -71,6 +71,9 @@ cudaError_t launch_build_wtab(float4 *tab, float beta, int32_t entries, cudaStre
 // sub-block in shared memory, logged rows applied at period ends.
 bool block_supported(int qtype, int k);
 cudaError_t launch_block(int qtype, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
+// pns_half.cu: Unbiased PNS, systematic sets of k <= 16, dense Q (hbytes 4), no
+// exchange, no producer warps: two chains per warp, 16 threads per chain.
+cudaError_t launch_half(int qtype, const KParams &P, int grid, int block, size_t smem, cudaStream_t s);
 int32_t block_chain_bytes(int32_t ld, int32_t k, int32_t hbytes, int32_t qbytes, int32_t R, int32_t W);
 // CTAs of the blocked kernel resident per SM at this shape (0 on error).
 int block_occupancy(int qtype, int threads, size_t smem);

@@ -51,7 +51,7 @@ class pns_info(C.Structure):
                 ("field_bytes", C.c_int32), ("field_is_float", C.c_int32), ("tape_capacity", C.c_int64),
                 ("warps_per_chain", C.c_int32), ("ctas", C.c_int32), ("team_warps", C.c_int32),
                 ("producer_warps", C.c_int32), ("spec_depth", C.c_int32), ("period_blocked", C.c_int32),
-                ("set_sweep", C.c_int32)]
+                ("set_sweep", C.c_int32), ("chains_per_warp", C.c_int32), ("reserved_info", C.c_int32)]
 
 
 class pns_moment_scalars(C.Structure):

@@ -16,7 +16,7 @@ namespace pnsk {
 namespace {
 
 template <typename QT, typename HT>
-__global__ void __launch_bounds__(512) pns_half_kernel(const KParams P) {
+__global__ void __launch_bounds__(512, 2) pns_half_kernel(const KParams P) {
     using A = Arith<HT>;
     using D = typename A::D;
     using CT = typename A::C;

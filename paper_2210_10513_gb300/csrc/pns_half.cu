@@ -59,11 +59,6 @@ __global__ void __launch_bounds__(512, 2) pns_half_kernel(const KParams P) {
     const float anneal_ls0 = P.anneal_steps > 0 ? det_logf(P.anneal_start) : 0.0f;
     __syncwarp(hm);
 
-    auto delta_of = [&](int i) -> D {
-        const bool xi = (xw[i >> 5] >> (i & 31)) & 1u;
-        return A::delta(h[i], bvec[i], dvec[i], xi);
-    };
-
     // tape and sums one record late (as the one-warp kernel)
     int64_t tape_pos = 0, rec_started = 0, sum_int = 0;
     int32_t pend_flip = 0;
@@ -88,6 +83,18 @@ __global__ void __launch_bounds__(512, 2) pns_half_kernel(const KParams P) {
         sum_int += mi;
     };
 
+    // The state-independent draws in batches across the half's lanes: lane
+    // hl draws the multiplicity's Exp(1) of record b16 + hl (16 records per
+    // batch), and the RACE block hl / 4 of record b4 + hl mod 4 (4 records
+    // per batch); a record takes its numbers from the lanes that drew them.
+    // The values are those of drawing each record's own numbers.
+    float e1_mine = 0.0f;
+    uint4 blk_mine = make_uint4(0u, 0u, 0u, 0u);
+    const int seg = threadIdx.x & 16;  // first lane of this half
+    // the position's bit index, b and diagonal, kept for the set (re-read
+    // when the set moves on)
+    int ci = 0, ci_set = -1;
+    CT b_ci = CT(0), d_ci = CT(0);
     for (int64_t r = 0; r < P.steps; ++r) {
         // tape = 2: the state this record starts from and its energy
         if (P.tape == 2 && rec_started < P.tape_cap) {
@@ -99,12 +106,22 @@ __global__ void __launch_bounds__(512, 2) pns_half_kernel(const KParams P) {
         rec_started += 1;
         const uint64_t step = static_cast<uint64_t>(st.step);
         const float beta = anneal_beta(beta_chain, anneal_ls0, P.anneal_steps, static_cast<int64_t>(step) + 1);
-        const float e1 = record_draws(seed, chain_id, step, n, false, true).e1;
+        const int r16 = static_cast<int>(r & 15), r4 = static_cast<int>(r & 3);
+        if (r16 == 0) e1_mine = record_draws(seed, chain_id, step + static_cast<uint64_t>(hl), n, false, true).e1;
+        if (r4 == 0)
+            blk_mine = rng_block(seed, TAG_RACE, chain_id, step + static_cast<uint64_t>(hl & 3),
+                                 static_cast<uint32_t>(hl >> 2));
+        const float e1 = __shfl_sync(hm, e1_mine, seg + r16);
         // deltas of the set (position hl), the anchor
         const int t = hl;
-        int ci = st.set_start + (t < k ? t : k - 1);
-        ci = ci >= n ? ci - n : ci;
-        const D dl = delta_of(ci);
+        if (st.set_start != ci_set) {
+            ci_set = st.set_start;
+            ci = st.set_start + (t < k ? t : k - 1);
+            ci = ci >= n ? ci - n : ci;
+            b_ci = bvec[ci];
+            d_ci = dvec[ci];
+        }
+        const D dl = A::delta(h[ci], b_ci, d_ci, (xw[ci >> 5] >> (ci & 31)) & 1u);
         const uint32_t kd = A::key(A::pos(dl));
         const uint32_t amin_k = __reduce_min_sync(hm, t < k ? kd : 0xFFFFFFFFu);
         const D amin = A::unkey(amin_k);
@@ -113,7 +130,12 @@ __global__ void __launch_bounds__(512, 2) pns_half_kernel(const KParams P) {
         const float anchor_f = af > 0.0f ? anchor_e : 1.0f;
         // weight, race key and quantised weight of the position: race word t
         // mod 4 of RACE block t / 4
-        const uint4 blk = rng_block(seed, TAG_RACE, chain_id, step, static_cast<uint32_t>(t >> 2));
+        const int src = seg + (hl & ~3) + r4;  // the lane that drew block t / 4 of this record
+        uint4 blk;
+        blk.x = __shfl_sync(hm, blk_mine.x, src);
+        blk.y = __shfl_sync(hm, blk_mine.y, src);
+        blk.z = __shfl_sync(hm, blk_mine.z, src);
+        blk.w = __shfl_sync(hm, blk_mine.w, src);
         const float ex = race_exp(pick_word(blk, static_cast<uint32_t>(t & 3)));
         const float w = det_expf(-__fmul_rn(beta, A::diff(A::pos(dl), amin)));
         const float ws = __fmul_rn(w, 65536.0f);
@@ -129,7 +151,7 @@ __global__ void __launch_bounds__(512, 2) pns_half_kernel(const KParams P) {
         int j = st.set_start + static_cast<int>(wpos);
         j = j >= n ? j - n : j;
         const Mult mu = multiplicity_e1(S, k, anchor_f, e1);
-        const D dj = delta_of(j);
+        const D dj = __shfl_sync(hm, dl, seg + static_cast<int>(wpos));  // the winner's delta
         __syncwarp(hm);  // reads of h and x are done
         if (mult_fits(mu, st.L)) {
             const int64_t mrec = mu.mi >= 0 ? mu.mi : static_cast<int64_t>(mult_md(mu));

@@ -541,6 +541,13 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
     // tape = 2: the state a record starts from (the jump-chain sample J that
     // its multiplicity weighs) and its energy
     int64_t rec_started = 0;
+    // Without producer warps the record scalars (the multiplicity's Exp(1),
+    // Metropolis' proposal and log-uniform) are drawn 32 records at a time,
+    // lane l drawing record b + l, and each record takes its own from that
+    // lane: the same values, one STEP block per lane per 32 records.
+    float bat_e1 = 0.0f, bat_mlu = 0.0f;
+    int32_t bat_mi = 0;
+    int bat_i = 32;
     auto sample_record = [&]() {
         if (P.tape == 2 && rec_started < P.tape_cap) {
             const int64_t o = static_cast<int64_t>(cid) * P.tape_cap + rec_started;
@@ -565,7 +572,18 @@ __global__ void __launch_bounds__(TC == 32 ? 1024 : 512) pns_sample_kernel(const
             rd.mi = reinterpret_cast<const int32_t *>(slot)[1];
             rd.mlu = reinterpret_cast<const float *>(slot)[2];
         } else {
-            rd = record_draws(seed, chain_id, step, n);
+            if (bat_i == 32) {
+                const RecordDraws d = record_draws(seed, chain_id, step + static_cast<uint64_t>(lane), n,
+                                                   variant == VAR_METROPOLIS, variant != VAR_METROPOLIS);
+                bat_e1 = d.e1;
+                bat_mi = d.mi;
+                bat_mlu = d.mlu;
+                bat_i = 0;
+            }
+            rd.e1 = __shfl_sync(0xFFFFFFFFu, bat_e1, bat_i);
+            rd.mi = __shfl_sync(0xFFFFFFFFu, bat_mi, bat_i);
+            rd.mlu = __shfl_sync(0xFFFFFFFFu, bat_mlu, bat_i);
+            bat_i += 1;
         }
         bool period_end = false;
         if (variant == VAR_METROPOLIS) {

@@ -382,11 +382,22 @@ __device__ __forceinline__ bool block_period(const KParams &P, const BlockChain<
     // weight e^{-beta A} in place of a candidate's.
     const bool anchor_lane = k <= 31 * PPL && lane == 31;
     int len = 0, nrec = 0;
-    const bool extra_step = k > 31 * PPL;  // (PPL 4, k > 124: every lane draws the Exp(1) from its own STEP block)
+    const bool extra_step = k > 31 * PPL;  // (PPL 4, k > 124: no lane is free for the STEP block)
+    // With extra_step the multiplicity's Exp(1) is drawn 32 records at a
+    // time, lane l drawing record e1_base + l (the same values).
+    float e1_bat = 0.0f;
+    int64_t e1_base = -64;
+    auto e1_of = [&](int64_t s) -> float {
+        if (s - e1_base >= 32) {
+            e1_base = s;
+            e1_bat = record_draws(seed, chain_id, static_cast<uint64_t>(s) + static_cast<uint64_t>(lane), n, false, true).e1;
+        }
+        return __shfl_sync(0xFFFFFFFFu, e1_bat, static_cast<int>(s - e1_base));
+    };
     float exq[4], e1q = 0.0f;  // (PPL 4) the current record's draws
     if (!BATCH) {
         lane_draws4(seed, chain_id, static_cast<uint64_t>(stp), lane, !extra_step && lane == 31, exq);
-        e1q = extra_step ? record_draws(seed, chain_id, static_cast<uint64_t>(stp), n, false, true).e1
+        e1q = extra_step ? e1_of(stp)
                          : __shfl_sync(0xFFFFFFFFu, exq[0], 31);
     }
     // deferred tape entry (written one record late).  The multiplicities
@@ -463,7 +474,7 @@ __device__ __forceinline__ bool block_period(const KParams &P, const BlockChain<
         if constexpr (!BATCH) {  // the next record's draws
             float xn[4];
             lane_draws4(seed, chain_id, step + 1, lane, !extra_step && lane == 31, xn);
-            e1q = extra_step ? record_draws(seed, chain_id, step + 1, n, false, true).e1 : xn[0];
+            e1q = extra_step ? e1_of(static_cast<int64_t>(step) + 1) : xn[0];
 #pragma unroll
             for (int u = 0; u < 4; ++u) exq[u] = xn[u];
         }

@@ -88,6 +88,47 @@ __global__ void __launch_bounds__(256) donuts_kernel(const pns_donuts_config cfg
     bool need_set = true;
     float dx = 0.0f, dy = 0.0f;
     double W = 0.0, sx[2] = {0.0, 0.0}, sx2[2] = {0.0, 0.0}, sx4[2] = {0.0, 0.0}, spos[2] = {0.0, 0.0};
+    // Unbiased: the multiplicity's Exp(1) drawn 32 records at a time, lane l
+    // drawing record b + l, each record taking its own from that lane (the
+    // same values)
+    float e1_bat = 0.0f;
+    // The per-record sums in batches of 32 records: lane l keeps record b + l
+    // (its multiplicity and state); at the batch end every lane forms its
+    // record's fp64 products at once and lane 0 adds them in record order
+    // (the additions, the only order-dependent part, stay sequential).
+    double my_m = 0.0;
+    float my_x1 = 0.0f, my_x2 = 0.0f;
+    auto flush_sums = [&](int cnt) {
+        const float mx[2] = {my_x1, my_x2};
+        double p1[2], p2[2], p4[2];
+        bool pz[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const double xd = static_cast<double>(mx[i]);
+            const double x2d = __dmul_rn(xd, xd);
+            p1[i] = __dmul_rn(my_m, xd);
+            p2[i] = __dmul_rn(my_m, x2d);
+            p4[i] = __dmul_rn(my_m, __dmul_rn(x2d, x2d));
+            pz[i] = xd > 0.0;
+        }
+        for (int l = 0; l < cnt; ++l) {
+            const double ml = __shfl_sync(0xFFFFFFFFu, my_m, l);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const double a = __shfl_sync(0xFFFFFFFFu, p1[i], l);
+                const double b = __shfl_sync(0xFFFFFFFFu, p2[i], l);
+                const double c = __shfl_sync(0xFFFFFFFFu, p4[i], l);
+                const bool pos = __shfl_sync(0xFFFFFFFFu, pz[i] ? 1 : 0, l) != 0;
+                if (lane == 0) {
+                    sx[i] = __dadd_rn(sx[i], a);
+                    sx2[i] = __dadd_rn(sx2[i], b);
+                    sx4[i] = __dadd_rn(sx4[i], c);
+                    if (pos) spos[i] = __dadd_rn(spos[i], ml);
+                }
+            }
+            if (lane == 0) W = __dadd_rn(W, ml);
+        }
+    };
     for (int64_t step = 0; step < steps; ++step) {
         const float e0 = donut_energy(cfg.mu0, cfg.c, x1, x2);
         double m;
@@ -154,8 +195,11 @@ __global__ void __launch_bounds__(256) donuts_kernel(const pns_donuts_config cfg
             const uint32_t SA = __reduce_add_sync(0xFFFFFFFFu, sa);
             const uint32_t SB = __reduce_add_sync(0xFFFFFFFFu, sb);
             const uint64_t S = (static_cast<uint64_t>(SA) << 16) + static_cast<uint64_t>(SB);
-            const uint4 sw = rng_block(seed, TAG_STEP, cid, static_cast<uint64_t>(step), 0);
-            const float e1 = -det_logf(u01_fine64((static_cast<uint64_t>(sw.y) << 32) | static_cast<uint64_t>(sw.x)));
+            if ((step & 31) == 0) {
+                const uint4 sw = rng_block(seed, TAG_STEP, cid, static_cast<uint64_t>(step + lane), 0);
+                e1_bat = -det_logf(u01_fine64((static_cast<uint64_t>(sw.y) << 32) | static_cast<uint64_t>(sw.x)));
+            }
+            const float e1 = __shfl_sync(0xFFFFFFFFu, e1_bat, static_cast<int>(step & 31));
             const Mult mu = multiplicity_e1(S, k, anchor_f, e1);
             const int wl = static_cast<int>(wpos >> 1);
             const float wdx = __shfl_sync(0xFFFFFFFFu, dx, wl);
@@ -178,23 +222,18 @@ __global__ void __launch_bounds__(256) donuts_kernel(const pns_donuts_config cfg
                 need_set = true;
             }
         }
-        if (lane == 0) {  // the record weighs the state it starts from
-            const float xs[2] = {x1, x2};
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const double xd = static_cast<double>(xs[i]);
-                const double x2d = __dmul_rn(xd, xd);
-                sx[i] = __dadd_rn(sx[i], __dmul_rn(m, xd));
-                sx2[i] = __dadd_rn(sx2[i], __dmul_rn(m, x2d));
-                sx4[i] = __dadd_rn(sx4[i], __dmul_rn(m, __dmul_rn(x2d, x2d)));
-                if (xd > 0.0) spos[i] = __dadd_rn(spos[i], m);
-            }
-            W = __dadd_rn(W, m);
+        // the record weighs the state it starts from
+        if (lane == static_cast<int>(step & 31)) {
+            my_m = m;
+            my_x1 = x1;
+            my_x2 = x2;
         }
+        if ((step & 31) == 31) flush_sums(32);
         moves += moved ? 1 : 0;
         x1 = nx1;
         x2 = nx2;
     }
+    if (steps & 31) flush_sums(static_cast<int>(steps & 31));
     if (lane == 0) {
         pns_donuts_stats st;
         memset(&st, 0, sizeof(st));

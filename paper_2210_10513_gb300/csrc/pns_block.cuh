@@ -71,6 +71,9 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) 
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async4_s(uint32_t smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_dst), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // The 16-byte chunks q = q0, q0 + dq, ... of Q columns for one chain: each
@@ -970,16 +973,29 @@ __global__ void __launch_bounds__(512) pns_block_kernel(const __grid_constant__ 
     // The set's sub-block, b and diagonal, by cp.async (4-byte entries) or
     // plain loads (2-byte entries).
     auto load_set = [&](int s) {
-        for (int a = wg; a < k; a += W) {  // row a of the sub-block by warp, columns by lane
+        // row a of the sub-block by warp, columns t = lane + 32 u (k <= 128)
+        // by lane: the lane's columns and the shared address once per set
+        int ct[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = s + lane + 32 * u;
+            ct[u] = c >= n ? c - n : c;
+        }
+        const uint32_t sub_s = static_cast<uint32_t>(__cvta_generic_to_shared(sub)) + 4u * static_cast<uint32_t>(lane);
+        for (int a = wg; a < k; a += W) {
             int ra = s + a;
             if (ra >= n) ra -= n;
             const QT *row = Q + static_cast<int64_t>(ra) * ld;
-            QT *dst = sub + a * kp;
-            for (int t = lane; t < k; t += 32) {
-                int ct = s + t;
-                if (ct >= n) ct -= n;
-                if constexpr (sizeof(QT) == 4) cp_async4(dst + t, row + ct);
-                else dst[t] = row[ct];
+            if constexpr (sizeof(QT) == 4) {
+                const uint32_t d0 = sub_s + 4u * static_cast<uint32_t>(a * kp);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (lane + 32 * u < k) cp_async4_s(d0 + 128u * u, row + ct[u]);
+            } else {
+                QT *dst = sub + a * kp;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (lane + 32 * u < k) dst[lane + 32 * u] = row[ct[u]];
             }
         }
         for (int t = gtid; t < k; t += GT) {

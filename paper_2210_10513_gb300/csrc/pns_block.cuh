@@ -33,7 +33,7 @@
 
 namespace pnsk {
 
-constexpr int APPLY_U = 8;  // logged rows in flight per thread
+constexpr int APPLY_U = 4;  // logged rows in flight per thread
 
 template <typename QT, typename HT>
 __device__ __forceinline__ HT add_elem(HT h, QT q, bool up) {
